@@ -1,0 +1,232 @@
+"""CPU oracle (TEST INFRASTRUCTURE ONLY).
+
+A plain FP64 C implementation of the batched BDF integrator, its right-hand
+sides, Jacobians and LU, loaded with ctypes.  Only ``tests/``,
+``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
+import this package; the CUDA library never calls it.
+
+Citations refer to arXiv 2405.01713 (Balos et al., "SUNDIALS Time
+Integrators for Exascale Applications with Many Independent ODE Systems").
+"""
+import ctypes
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "liboracle.so")
+
+ROBERTSON, MECHANISM, COSMOLOGY, LINEAR = 0, 1, 2, 3
+SUCCESS, TOO_MUCH_WORK, ERR_FAILURE, CONV_FAILURE, H_TOO_SMALL, NONFINITE = 0, -1, -3, -4, -5, -6
+STAT_FIELDS = ("nst", "nfe", "nje", "nni", "ncf", "nef", "qlast", "status")
+
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("n", ctypes.c_int), ("nparams", ctypes.c_int),
+                ("params", _dp), ("K", ctypes.c_int), ("M", ctypes.c_int),
+                ("W", _dp), ("nasa", _dp), ("lnA", _dp), ("beta", _dp), ("Ea", _dp),
+                ("react", _ip), ("prod", _ip), ("nknots", ctypes.c_int),
+                ("lnT", _dp), ("lnLam", _dp), ("gamma_heat", ctypes.c_double)]
+
+
+class Options(ctypes.Structure):
+    _fields_ = [("rtol", ctypes.c_double), ("atol", _dp), ("max_steps", ctypes.c_int),
+                ("max_order", ctypes.c_int), ("jac_mode", ctypes.c_int)]
+
+
+def build(force=False):
+    """Compile liboracle.so with gcc (plain -O2, OpenMP over cells)."""
+    src = [os.path.join(HERE, f) for f in ("oracle.c", "rhs_impl.h", "oracle.h")]
+    if not force and os.path.exists(LIB_PATH) and \
+            os.path.getmtime(LIB_PATH) >= max(os.path.getmtime(s) for s in src):
+        return LIB_PATH
+    cmd = ["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
+           os.path.join(HERE, "oracle.c"), "-o", LIB_PATH + ".tmp", "-lm"]
+    subprocess.check_call(cmd)
+    os.replace(LIB_PATH + ".tmp", LIB_PATH)
+    return LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        build()
+        L = ctypes.CDLL(LIB_PATH)
+        PP = ctypes.POINTER(Problem)
+        L.orc_rhs.argtypes = [PP, ctypes.c_long, _dp, _dp]
+        L.orc_jac.argtypes = [PP, ctypes.c_long, _dp, _dp, _dp, ctypes.c_int, _dp]
+        L.orc_lu_factor.argtypes = [ctypes.c_int, _dp, _ip]
+        L.orc_lu_factor.restype = ctypes.c_int
+        L.orc_lu_solve.argtypes = [ctypes.c_int, _dp, _ip, _dp]
+        L.orc_bdf_l.argtypes = [ctypes.c_int, _dp, _dp]
+        L.orc_error_constant.argtypes = [ctypes.c_int, _dp]
+        L.orc_error_constant.restype = ctypes.c_double
+        L.orc_order_decrease.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp]
+        L.orc_order_increase.argtypes = [ctypes.c_int, ctypes.c_int, _dp, _dp, _dp, ctypes.c_double]
+        L.orc_integrate.argtypes = [PP, ctypes.c_long, _dp, ctypes.c_double, ctypes.c_double,
+                                    ctypes.POINTER(Options), _ip, _dp, ctypes.c_int]
+        L.orc_integrate.restype = ctypes.c_int
+        L.orc_num_threads.restype = ctypes.c_int
+        L.orc_bdf_fixed.argtypes = [PP, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_int,
+                                    _dp, _dp, _dp, _dp, _dp]
+        L.orc_bdf_fixed.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _d(a):
+    return a.ctypes.data_as(_dp)
+
+
+def _i(a):
+    return a.ctypes.data_as(_ip)
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+class OracleProblem:
+    """Holds the numpy arrays a Problem struct points into (keeps them alive)."""
+
+    def __init__(self, kind, n, params, mech=None, table=None):
+        self.kind, self.n = kind, n
+        self.params = _f64(params).reshape(params.shape[0], -1)
+        self.s = Problem()
+        self.s.kind, self.s.n = kind, n
+        self.s.nparams = self.params.shape[1]
+        self.s.params = _d(self.params)
+        if mech is not None:
+            self.W, self.nasa = _f64(mech.W), _f64(mech.nasa)
+            self.lnA, self.beta, self.Ea = _f64(mech.lnA), _f64(mech.beta), _f64(mech.Ea)
+            self.react = np.ascontiguousarray(mech.react, dtype=np.int32)
+            self.prod = np.ascontiguousarray(mech.prod, dtype=np.int32)
+            self.s.K, self.s.M = mech.n_species, mech.n_reactions
+            self.s.W, self.s.nasa = _d(self.W), _d(self.nasa)
+            self.s.lnA, self.s.beta, self.s.Ea = _d(self.lnA), _d(self.beta), _d(self.Ea)
+            self.s.react, self.s.prod = _i(self.react), _i(self.prod)
+        if table is not None:
+            self.lnT, self.lnLam = _f64(table.lnT), _f64(table.lnLam)
+            self.s.nknots = len(self.lnT)
+            self.s.lnT, self.s.lnLam = _d(self.lnT), _d(self.lnLam)
+            self.s.gamma_heat = table.gamma_heat
+
+    @property
+    def ref(self):
+        return ctypes.byref(self.s)
+
+
+def problem_from_workload(w, cells=None):
+    """OracleProblem for a workload dict of ``synth.workloads``."""
+    params = w["params"] if cells is None else w["params"][cells]
+    if w["kind"] == "robertson":
+        return OracleProblem(ROBERTSON, 3, params)
+    if w["kind"] == "mechanism":
+        return OracleProblem(MECHANISM, w["mech"].n_vars, params, mech=w["mech"])
+    if w["kind"] == "cosmology":
+        return OracleProblem(COSMOLOGY, 1, params, table=w["table"])
+    raise ValueError(w["kind"])
+
+
+def linear_problem(A):
+    """y' = A_c y per cell, A: [C, n, n]."""
+    A = _f64(A)
+    return OracleProblem(LINEAR, A.shape[1], A.reshape(A.shape[0], -1))
+
+
+def rhs(pb, y, cell=0):
+    y = _f64(y)
+    f = np.empty(pb.n)
+    lib().orc_rhs(pb.ref, cell, _d(y), _d(f))
+    return f
+
+
+def jac(pb, y, cell=0, mode=0, w=None):
+    """Dense J = df/dy; mode 0 complex step, 1 forward difference."""
+    y = _f64(y)
+    f = rhs(pb, y, cell)
+    w = np.ones(pb.n) if w is None else _f64(w)
+    J = np.empty((pb.n, pb.n))
+    lib().orc_jac(pb.ref, cell, _d(y), _d(f), _d(w), mode, _d(J))
+    return J
+
+
+def lu_factor(A):
+    A = _f64(A).copy()
+    n = A.shape[0]
+    piv = np.empty(n, dtype=np.int32)
+    info = lib().orc_lu_factor(n, _d(A), _i(piv))
+    return A, piv, info
+
+
+def lu_solve(LU, piv, b):
+    b = _f64(b).copy()
+    lib().orc_lu_solve(LU.shape[0], _d(_f64(LU)), _i(np.ascontiguousarray(piv, np.int32)), _d(b))
+    return b
+
+
+def bdf_l(xi):
+    xi = _f64(xi)
+    q = len(xi)
+    l = np.empty(q + 1)
+    lib().orc_bdf_l(q, _d(xi), _d(l))
+    return l
+
+
+def error_constant(q, xi):
+    return lib().orc_error_constant(q, _d(_f64(xi)))
+
+
+def order_decrease(z, nodes):
+    z = _f64(z).copy()
+    q = z.shape[0] - 1
+    lib().orc_order_decrease(q, z.shape[1], _d(z), _d(_f64(nodes)))
+    return z[:q]
+
+
+def order_increase(z, acor, l, xi_qp1):
+    q = z.shape[0] - 1
+    zz = np.zeros((q + 2, z.shape[1]))
+    zz[:q + 1] = z
+    lib().orc_order_increase(q, z.shape[1], _d(zz), _d(_f64(acor)), _d(_f64(l)), xi_qp1)
+    return zz
+
+
+def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
+              jac_mode=0, nthreads=0):
+    """Integrate every cell of pb from t0 to tout.
+
+    Returns (y, stats, hlast, worst_status); stats is a structured view with
+    the fields of STAT_FIELDS."""
+    y = _f64(y0).copy().reshape(-1, pb.n)
+    C = y.shape[0]
+    atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
+    o = Options(rtol, _d(atol), max_steps, max_order, jac_mode)
+    st = np.zeros((C, 8), dtype=np.int32)
+    hl = np.zeros(C)
+    worst = lib().orc_integrate(pb.ref, C, _d(y), t0, tout, ctypes.byref(o), _i(st), _d(hl), nthreads)
+    return y, st, hl, worst
+
+
+def bdf_fixed(pb, q, h, nsteps, zinit, hist, cell=0):
+    zinit = _f64(zinit)
+    hist6 = np.zeros(6)
+    hist6[:len(hist)] = hist
+    y = np.empty(pb.n)
+    dl = np.empty(pb.n)
+    est = np.empty(pb.n)
+    rc = lib().orc_bdf_fixed(pb.ref, cell, q, h, nsteps, _d(zinit), _d(hist6), _d(y), _d(dl), _d(est))
+    if rc:
+        raise RuntimeError("singular Newton matrix")
+    return y, dl, est
+
+
+def num_threads():
+    return lib().orc_num_threads()

@@ -1,0 +1,575 @@
+/* CPU oracle for the batched BDF integrator: TEST INFRASTRUCTURE ONLY.
+ *
+ * Plain C, FP64, one cell at a time (OpenMP only distributes independent
+ * cells).  Only the tests, smoke() and the benchmark's CPU-baseline leg may
+ * load it; the CUDA library shares no code with it.
+ *
+ * The method (arXiv 2405.01713, Sec. 2): each cell's ODE y' = f(t, y; p)
+ * (Eq. 1) is advanced by an adaptive-order (1..5), adaptive-step linear
+ * multistep (BDF) method of the CVODE kind.  A step is accepted when the WRMS
+ * norm (Eq. wrms) of its local-truncation-error estimate is below one;
+ * otherwise the step is cut and, possibly, the order lowered.  The implicit
+ * corrector is solved by a modified Newton iteration with the stopping test
+ * of Eq. stop_newton (c_eps = 0.1, c_r = 0.3), on the matrix I - gamma J with
+ * a dense Jacobian (solution approaches 2A/3A of Table 1) factored by LU with
+ * partial pivoting (Sec. 4.1.6), reused across iterations and steps until
+ * the iteration diverges (Sec. 3.1).
+ *
+ * The paper does not print the BDF internals; the readings used here are:
+ *  - Nordsieck history z_j = h^j y^(j)/j!, predicted by the Pascal-triangle
+ *    sums, corrected by z += l * Delta, where l are the coefficients of
+ *    Lambda(x) = prod_{i=1..q} (1 + x/xi_i), xi_i = (t_n - t_{n-i})/h_n
+ *    (the variable-coefficient form: the corrected polynomial interpolates
+ *    y_n and the q previous solution values);
+ *  - local error estimate E = Delta / (1 + l_1 xi_{q+1}), exact for a
+ *    solution that is a polynomial of degree q+1 when f does not depend on y;
+ *  - Newton tolerance: R ||delta|| < 0.1 / C_q with C_q = 1/(1 + l_1 xi_{q+1})
+ *    (the correction may use a tenth of the error-test budget); at most 3
+ *    iterations, divergence when ||delta_m|| > 2 ||delta_{m-1}||; R starts
+ *    at 1 in every Newton solve (it estimates the rate of the current
+ *    iteration; carrying it over from earlier steps let unconverged first
+ *    corrections pass the test and pollute the error estimate);
+ *  - matrix rebuild (fresh J, M = I - gamma J, LU) when 20 steps have passed
+ *    since the last one, when |gamma/gamma_M - 1| > 0.3, or after a Newton
+ *    failure; a stale matrix scales each correction by 2/(1 + gamma/gamma_M);
+ *  - step factors eta_p = 1/((b_p ||E_p||)^(1/(p+1)) + 1e-6) with biases
+ *    6 (q-1), 6 (q), 10 (q+1); no change below 1.5; growth capped at 1e4 on
+ *    the first step and 10 afterwards, and at 1 right after a failed attempt;
+ *    order changes considered after q+1 steps at the current order;
+ *  - error-test failure: eta in [0.1, 0.9], lower order when that allows a
+ *    larger step; from the third failure of a step, eta = 0.1 and a restart
+ *    at order 1; seven failures end the cell (ERR_FAILURE); Newton failure:
+ *    eta = 0.25, ten per step end the cell (CONV_FAILURE);
+ *  - first step from the starting-step algorithm of Hairer, Norsett and
+ *    Wanner (Solving ODEs I, Sec. II.4) with the WRMS norm;
+ *  - every call is a cold start at order 1 and lands exactly on tout.
+ */
+#include <complex.h>
+#include <float.h>
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+#include "oracle.h"
+
+#define EXPORT __attribute__((visibility("default")))
+#define QMAX 5
+
+/* ---- right-hand sides: real and complex instances -------------------- */
+#define REAL double
+#define FN(x) x##_r
+#define RE(x) (x)
+#define EXPF exp
+#define LOGF log
+#include "rhs_impl.h"
+#undef REAL
+#undef FN
+#undef RE
+#undef EXPF
+#undef LOGF
+
+#define REAL double complex
+#define FN(x) x##_c
+#define RE(x) creal(x)
+#define EXPF cexp
+#define LOGF clog
+#include "rhs_impl.h"
+#undef REAL
+#undef FN
+#undef RE
+#undef EXPF
+#undef LOGF
+
+EXPORT void orc_rhs(const orc_problem *pb, long cell, const double *y, double *f)
+{
+    rhs_r(pb, cell, y, f);
+}
+
+/* Dense Jacobian J[i*n + j] = d f_i / d y_j.
+ * mode 0: complex step, J e_j = Im f(y + i s e_j) / s with s = 1e-30 (no
+ * subtractive cancellation, so exact to rounding);
+ * mode 1: forward difference quotient (the numerical Jacobian of solution
+ * approaches 3A/3B, Table 1) with increment max(sqrt(eps)|y_j|, sqrt(eps)/w_j). */
+EXPORT void orc_jac(const orc_problem *pb, long cell, const double *y,
+                    const double *f0, const double *w, int mode, double *J)
+{
+    const int n = pb->n;
+    if (mode == 0) {
+        double complex yc[n], fc[n];
+        const double s = 1e-30;
+        for (int j = 0; j < n; ++j) {
+            for (int k = 0; k < n; ++k) yc[k] = y[k];
+            yc[j] = y[j] + I * s;
+            rhs_c(pb, cell, yc, fc);
+            for (int i = 0; i < n; ++i) J[i * n + j] = cimag(fc[i]) / s;
+        }
+    } else {
+        double yp[n], fp[n];
+        const double se = sqrt(DBL_EPSILON);
+        for (int j = 0; j < n; ++j) {
+            memcpy(yp, y, sizeof(double) * n);
+            double inc = fmax(se * fabs(y[j]), se / w[j]);
+            yp[j] = y[j] + inc;
+            inc = yp[j] - y[j];
+            rhs_r(pb, cell, yp, fp);
+            for (int i = 0; i < n; ++i) J[i * n + j] = (fp[i] - f0[i]) / inc;
+        }
+    }
+}
+
+/* ---- dense LU with partial pivoting (Sec. 4.1.6, "dense direct") ----------
+ * Row pivoting, pivot = the first row of largest magnitude in the column.
+ * piv[k] is the row exchanged with row k at elimination step k.  Returns 0,
+ * or k+1 when column k has no nonzero pivot. */
+EXPORT int orc_lu_factor(int n, double *A, int32_t *piv)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = k;
+        double amax = fabs(A[k * n + k]);
+        for (int i = k + 1; i < n; ++i)
+            if (fabs(A[i * n + k]) > amax) { amax = fabs(A[i * n + k]); p = i; }
+        piv[k] = p;
+        if (amax == 0.0) return k + 1;
+        if (p != k)
+            for (int j = 0; j < n; ++j) {
+                double t = A[k * n + j]; A[k * n + j] = A[p * n + j]; A[p * n + j] = t;
+            }
+        for (int i = k + 1; i < n; ++i) {
+            double lik = A[i * n + k] / A[k * n + k];
+            A[i * n + k] = lik;
+            for (int j = k + 1; j < n; ++j) A[i * n + j] -= lik * A[k * n + j];
+        }
+    }
+    return 0;
+}
+
+EXPORT void orc_lu_solve(int n, const double *LU, const int32_t *piv, double *b)
+{
+    for (int k = 0; k < n; ++k) {
+        int p = piv[k];
+        if (p != k) { double t = b[k]; b[k] = b[p]; b[p] = t; }
+    }
+    for (int i = 1; i < n; ++i)
+        for (int j = 0; j < i; ++j) b[i] -= LU[i * n + j] * b[j];
+    for (int i = n - 1; i >= 0; --i) {
+        for (int j = i + 1; j < n; ++j) b[i] -= LU[i * n + j] * b[j];
+        b[i] /= LU[i * n + i];
+    }
+}
+
+/* ---- BDF coefficient algebra ------------------------------------------ */
+
+/* xi[i-1] = xi_i = (t_n - t_{n-i}) / h for i = 1..m, from the current step h
+ * and the previous accepted step sizes hist[0] = h_{n-1}, hist[1] = h_{n-2}..
+ * (zero where the history does not reach: a repeated node, i.e. the Taylor
+ * start). */
+static void bdf_xi(int m, double h, const double *hist, double *xi)
+{
+    double s = h;
+    xi[0] = 1.0;
+    for (int i = 1; i < m; ++i) { s += hist[i - 1]; xi[i] = s / h; }
+}
+
+/* l[0..q]: coefficients of Lambda(x) = prod_{i=1..q} (1 + x/xi_i). */
+EXPORT void orc_bdf_l(int q, const double *xi, double *l)
+{
+    l[0] = 1.0;
+    for (int j = 1; j <= q; ++j) l[j] = 0.0;
+    for (int i = 0; i < q; ++i)
+        for (int j = i + 1; j >= 1; --j) l[j] += l[j - 1] / xi[i];
+}
+
+/* C_q = 1 / (1 + l_1 xi_{q+1}): the estimate E = C_q Delta. */
+EXPORT double orc_error_constant(int q, const double *xi)
+{
+    double l[QMAX + 2];
+    orc_bdf_l(q, xi, l);
+    return 1.0 / (1.0 + l[1] * xi[q]);
+}
+
+/* Lower the order of the Nordsieck array z (columns 0..q, n values each) by
+ * one, keeping the polynomial's values at x = 0 and x = -nodes[i],
+ * i < q-1: subtract z_q * x * prod_{i<q-1} (x + nodes[i]). */
+EXPORT void orc_order_decrease(int q, int n, double *z, const double *nodes)
+{
+    double e[QMAX + 1] = {1.0, 0, 0, 0, 0, 0};
+    for (int i = 0; i < q - 1; ++i) {
+        for (int j = i + 1; j >= 1; --j) e[j] = e[j - 1] + e[j] * nodes[i];
+        e[0] *= nodes[i];
+    }
+    for (int j = 1; j < q; ++j)
+        for (int k = 0; k < n; ++k) z[j * n + k] -= e[j - 1] * z[q * n + k];
+    for (int k = 0; k < n; ++k) z[q * n + k] = 0.0;
+}
+
+/* Raise the order by one after a step at order q with correction acor and
+ * corrector coefficients l: add acor * (x/xi_{q+1}) * Lambda(x), the degree
+ * q+1 term that makes the polynomial also interpolate y_{n-q-1}. */
+EXPORT void orc_order_increase(int q, int n, double *z, const double *acor,
+                               const double *l, double xi_qp1)
+{
+    for (int k = 0; k < n; ++k) z[(q + 1) * n + k] = 0.0;
+    for (int j = 1; j <= q + 1; ++j)
+        for (int k = 0; k < n; ++k) z[j * n + k] += acor[k] * l[j - 1] / xi_qp1;
+}
+
+/* ---- vector helpers ---------------------------------------------------- */
+static double wrms(int n, const double *v, const double *w)
+{
+    double s = 0.0;
+    for (int i = 0; i < n; ++i) { double t = v[i] * w[i]; s += t * t; }
+    return sqrt(s / n);
+}
+
+static void set_weights(int n, const double *y, double rtol, const double *atol, double *w)
+{
+    for (int i = 0; i < n; ++i) w[i] = 1.0 / (rtol * fabs(y[i]) + atol[i]);
+}
+
+static int all_finite(int n, const double *v)
+{
+    for (int i = 0; i < n; ++i) if (!isfinite(v[i])) return 0;
+    return 1;
+}
+
+static void rescale(int q, int n, double *z, double eta)
+{
+    double f = 1.0;
+    for (int j = 1; j <= q; ++j) {
+        f *= eta;
+        for (int k = 0; k < n; ++k) z[j * n + k] *= f;
+    }
+}
+
+static double eta_from(double dsm, int p, double bias)
+{
+    return 1.0 / (pow(bias * dsm, 1.0 / (p + 1)) + 1e-6);
+}
+
+/* Matrix set-up: J at (t, y), M = I - gamma J, LU. Returns 0 on success. */
+static int setup_matrix(const orc_problem *pb, long cell, const double *y,
+                        const double *w, int jac_mode, double gamma,
+                        double *M, int32_t *piv, double *ftmp)
+{
+    const int n = pb->n;
+    if (jac_mode == 1) rhs_r(pb, cell, y, ftmp);
+    orc_jac(pb, cell, y, ftmp, w, jac_mode, M);
+    for (int i = 0; i < n * n; ++i) M[i] = -gamma * M[i];
+    for (int i = 0; i < n; ++i) M[i * n + i] += 1.0;
+    if (!all_finite(n * n, M)) return -1;
+    return orc_lu_factor(n, M, piv) ? -1 : 0;
+}
+
+/* Starting step of Hairer, Norsett & Wanner (Solving ODEs I, II.4), order 1,
+ * with the WRMS norm of Eq. wrms; bounded by the interval length. */
+static double initial_step(const orc_problem *pb, long cell, double t0, double tout,
+                           const double *y0, const double *f0, const double *w,
+                           double *ytmp, double *ftmp, int *nfe)
+{
+    const int n = pb->n;
+    const double span = tout - t0;
+    double d0 = wrms(n, y0, w), d1 = wrms(n, f0, w);
+    double h0 = (d0 < 1e-5 || d1 < 1e-5) ? 1e-6 * span : 0.01 * d0 / d1;
+    if (h0 > span) h0 = span;
+    for (int i = 0; i < n; ++i) ytmp[i] = y0[i] + h0 * f0[i];
+    rhs_r(pb, cell, ytmp, ftmp);
+    ++*nfe;
+    for (int i = 0; i < n; ++i) ytmp[i] = (ftmp[i] - f0[i]) / h0;
+    double d2 = wrms(n, ytmp, w);
+    double dm = fmax(d1, d2);
+    double h1 = (dm <= 1e-15) ? fmax(1e-6 * span, h0 * 1e-3) : sqrt(0.01 / dm);
+    double h = fmin(100.0 * h0, h1);
+    if (!(h > 0.0)) h = 1e-6 * span;
+    return fmin(h, span);
+}
+
+/* Optional per-step record for the discrete adjoint. */
+typedef struct {
+    int cap, count;
+    double *t, *h, *y;     /* accepted step end time, size, state [count, n] */
+    int *q;
+} step_log;
+
+/* ---- one cell, one call: t0 -> tout ------------------------------------- */
+static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
+                    double tout, const orc_options *op, orc_stats *st,
+                    double *hlast)
+{
+    const int n = pb->n;
+    const int qmax = op->max_order < 1 ? 1 : (op->max_order > QMAX ? QMAX : op->max_order);
+    double *z = calloc((size_t)(QMAX + 2) * n, sizeof(double));
+    double *zsave = calloc((size_t)(QMAX + 2) * n, sizeof(double));
+    double *M = malloc(sizeof(double) * n * n);
+    int32_t *piv = malloc(sizeof(int32_t) * n);
+    double *w = malloc(sizeof(double) * n), *f = malloc(sizeof(double) * n);
+    double *acor = malloc(sizeof(double) * n), *ycur = malloc(sizeof(double) * n);
+    double *del = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
+    double *tmp2 = malloc(sizeof(double) * n), *ksave = malloc(sizeof(double) * n);
+
+    orc_stats s = {0, 0, 0, 0, 0, 0, 1, ORC_SUCCESS};
+    double t = t0, h = 0.0;
+    int q = 1, qwait = 2, have_M = 0, force_setup = 1, nst_lastsetup = 0;
+    int have_ksave = 0;
+    double hist[QMAX + 1] = {0}, gamma_M = 0.0, R = 1.0, etamax = 1e4, h_ksave = 0.0;
+
+    if (!(tout > t0)) goto done_copy;
+    memcpy(z, y, sizeof(double) * n);
+    rhs_r(pb, cell, y, f);
+    s.nfe++;
+    if (!all_finite(n, f) || !all_finite(n, y)) { s.status = ORC_NONFINITE; goto done_copy; }
+    set_weights(n, y, op->rtol, op->atol, w);
+    h = initial_step(pb, cell, t0, tout, y, f, w, ycur, tmp, &s.nfe);
+    for (int k = 0; k < n; ++k) z[n + k] = h * f[k];
+
+    while (t < tout) {
+        if (s.nst >= op->max_steps) { s.status = ORC_TOO_MUCH_WORK; break; }
+        /* land exactly on tout: clip a step that would reach or pass it */
+        int last = 0;
+        if (t + h >= tout || tout - (t + h) <= 4.0 * DBL_EPSILON * fabs(tout)) {
+            double hn = tout - t;
+            rescale(q, n, z, hn / h);
+            h = hn;
+            last = 1;
+        }
+        set_weights(n, z, op->rtol, op->atol, w);   /* Eq. wrms: w from y^{n-1} */
+        int ncf = 0, nef = 0;
+        double dsm = 0.0, Cq = 0.0, l[QMAX + 2], xi[QMAX + 2];
+        for (;;) {  /* attempts */
+            memcpy(zsave, z, sizeof(double) * (q + 1) * n);
+            for (int k = 0; k < q; ++k)               /* predict */
+                for (int j = q; j > k; --j)
+                    for (int i = 0; i < n; ++i) z[(j - 1) * n + i] += z[j * n + i];
+            bdf_xi(q + 1, h, hist, xi);
+            orc_bdf_l(q, xi, l);
+            const double l1 = l[1], gamma = h / l1;
+            Cq = 1.0 / (1.0 + l1 * xi[q]);
+            int fresh = 0, conv = 0;
+            if (force_setup || !have_M || s.nst >= nst_lastsetup + 20 ||
+                fabs(gamma / gamma_M - 1.0) > 0.3) {
+                have_M = setup_matrix(pb, cell, z, w, op->jac_mode, gamma, M, piv, tmp) == 0;
+                s.nje++;
+                gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; force_setup = 0;
+            }
+            for (;;) {  /* Newton on G(y) = y - gamma f(tn, y) - a_n, a_n = z0 - z1/l1 */
+                conv = 0;
+                if (!have_M) break;
+                for (int i = 0; i < n; ++i) { acor[i] = 0.0; ycur[i] = z[i]; }
+                double delp = 0.0;
+                R = 1.0;
+                for (int m = 0;; ++m) {
+                    rhs_r(pb, cell, ycur, f);
+                    s.nfe++; s.nni++;
+                    for (int i = 0; i < n; ++i) del[i] = (h * f[i] - z[n + i]) / l1 - acor[i];
+                    orc_lu_solve(n, M, piv, del);
+                    if (gamma != gamma_M) {
+                        double c = 2.0 / (1.0 + gamma / gamma_M);
+                        for (int i = 0; i < n; ++i) del[i] *= c;
+                    }
+                    for (int i = 0; i < n; ++i) { acor[i] += del[i]; ycur[i] = z[i] + acor[i]; }
+                    double dn = wrms(n, del, w);
+                    if (!isfinite(dn)) break;
+                    if (m > 0) R = fmax(0.3 * R, dn / delp);
+                    if (R * dn * Cq < 0.1) { conv = 1; break; }  /* Eq. stop_newton */
+                    if (m + 1 == 3 || (m > 0 && dn > 2.0 * delp)) break;
+                    delp = dn;
+                }
+                if (conv || fresh) break;
+                /* stale matrix: rebuild at the predicted state and retry */
+                have_M = setup_matrix(pb, cell, z, w, op->jac_mode, gamma, M, piv, tmp) == 0;
+                s.nje++;
+                gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1;
+            }
+            if (!conv) {  /* Newton failure */
+                memcpy(z, zsave, sizeof(double) * (q + 1) * n);
+                s.ncf++; ncf++;
+                if (ncf >= 10) { s.status = ORC_CONV_FAILURE; break; }
+                h *= 0.25; rescale(q, n, z, 0.25);
+                force_setup = 1; etamax = 1.0; last = 0;
+                if (t + h == t) { s.status = ORC_H_TOO_SMALL; break; }
+                continue;
+            }
+            dsm = Cq * wrms(n, acor, w);
+            if (dsm < 1.0) break;   /* accept: ||LTE|| < 1 (Eq. wrms) */
+            /* error-test failure */
+            memcpy(z, zsave, sizeof(double) * (q + 1) * n);
+            s.nef++; nef++;
+            if (nef >= 7) { s.status = ORC_ERR_FAILURE; break; }
+            double eta;
+            if (nef < 3) {
+                eta = eta_from(dsm, q, 6.0);
+                int newq = q;
+                if (q > 1) {
+                    double l1m = 0.0, pm = 1.0;
+                    for (int i = 0; i < q - 1; ++i) { l1m += 1.0 / xi[i]; pm *= xi[i]; }
+                    double em = eta_from(wrms(n, z + q * n, w) * pm / l1m, q - 1, 6.0);
+                    if (em > eta) { eta = em; newq = q - 1; }
+                }
+                eta = fmin(0.9, fmax(0.1, eta));
+                if (newq < q) {
+                    double nodes[QMAX], sacc = 0.0;
+                    for (int i = 0; i < q - 1; ++i) { sacc += hist[i]; nodes[i] = sacc / h; }
+                    orc_order_decrease(q, n, z, nodes);
+                    q = newq; qwait = q + 1;
+                }
+                h *= eta; rescale(q, n, z, eta);
+            } else {
+                eta = 0.1;
+                h *= eta;
+                rhs_r(pb, cell, z, f);
+                s.nfe++;
+                for (int j = 2; j <= QMAX; ++j) for (int i = 0; i < n; ++i) z[j * n + i] = 0.0;
+                for (int i = 0; i < n; ++i) z[n + i] = h * f[i];
+                for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
+                q = 1; qwait = 2; have_ksave = 0;
+            }
+            etamax = 1.0; last = 0;
+            if (t + h == t) { s.status = ORC_H_TOO_SMALL; break; }
+        }
+        if (s.status != ORC_SUCCESS) break;
+
+        /* accepted step */
+        s.nst++;
+        t = last ? tout : t + h;
+        for (int j = 0; j <= q; ++j)
+            for (int i = 0; i < n; ++i) z[j * n + i] += l[j] * acor[i];
+        for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
+        hist[0] = h;
+        if (last) break;
+
+        /* step size and order for the next step */
+        qwait--;
+        const double l1 = l[1];
+        double eta = eta_from(dsm, q, 6.0);
+        int newq = q;
+        /* scaled (q+1)-th derivative estimate h^{q+1} y^{(q+1)}/(q+1)! */
+        const double kfac = l1 * l[q] / (1.0 + l1 * xi[q]);
+        if (qwait == 0) {
+            double em = 0.0, ep = 0.0;
+            if (q > 1) {
+                double l1m = 0.0, pm = 1.0;
+                for (int i = 0; i < q - 1; ++i) { l1m += 1.0 / xi[i]; pm *= xi[i]; }
+                em = eta_from(wrms(n, z + q * n, w) * pm / l1m, q - 1, 6.0);
+            }
+            if (q < qmax && have_ksave) {
+                double rq = pow(h / h_ksave, q + 1), pp = 1.0, l1p = l1 + 1.0 / xi[q];
+                for (int i = 0; i <= q; ++i) pp *= xi[i];
+                for (int i = 0; i < n; ++i) tmp2[i] = (kfac * acor[i] - rq * ksave[i]) / (q + 2);
+                ep = eta_from(wrms(n, tmp2, w) * pp / l1p, q + 1, 10.0);
+            }
+            if (em > eta && em >= ep) { eta = em; newq = q - 1; }
+            else if (ep > eta) { eta = ep; newq = q + 1; }
+        }
+        if (eta < 1.5) { eta = 1.0; newq = q; }
+        else eta = fmin(eta, etamax);
+        if (newq == q + 1) orc_order_increase(q, n, z, acor, l, xi[q]);
+        else if (newq == q - 1) orc_order_decrease(q, n, z, xi);
+        if (newq != q || qwait == 0) { q = newq; qwait = q + 1; have_ksave = 0; }
+        if (qwait == 1 && q < qmax) {
+            for (int i = 0; i < n; ++i) ksave[i] = kfac * acor[i];
+            h_ksave = h; have_ksave = 1;
+        }
+        h *= eta;
+        rescale(q, n, z, eta);
+        etamax = 10.0;
+    }
+    memcpy(y, z, sizeof(double) * n);
+    s.qlast = q;
+    goto done;
+done_copy:
+    s.qlast = q;
+done:
+    if (st) *st = s;
+    if (hlast) *hlast = h;
+    free(z); free(zsave); free(M); free(piv); free(w); free(f); free(acor);
+    free(ycur); free(del); free(tmp); free(tmp2); free(ksave);
+    return s.status;
+}
+
+/* Integrate ncells independent cells from t0 to tout (Sec. 2: one ODE
+ * system per cell, all over the same outer interval dt_CFD).  y is
+ * [ncells, n] (cell-contiguous "CY" order, Sec. 4.1.2).  Returns the most
+ * negative per-cell status. */
+EXPORT int orc_integrate(const orc_problem *pb, long ncells, double *y, double t0,
+                         double tout, const orc_options *op, orc_stats *stats,
+                         double *hlast, int nthreads)
+{
+    int worst = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 4) reduction(min : worst)
+    for (long c = 0; c < ncells; ++c) {
+        int r = bdf_cell(pb, c, y + (size_t)c * pb->n, t0, tout, op,
+                         stats ? stats + c : NULL, hlast ? hlast + c : NULL);
+        if (r < worst) worst = r;
+    }
+    return worst;
+}
+
+EXPORT int orc_num_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
+}
+
+/* Fixed step size, fixed order q: nsteps steps of size h from a given
+ * Nordsieck array zinit ((q+1) x n) and step history (previous step sizes,
+ * 6 entries), each corrector solved by full Newton to rounding level.
+ * Returns y at the end, and for the last step the correction Delta and the
+ * estimate E = C_q Delta.  Used to pin coefficients, order and estimate. */
+EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int nsteps,
+                         const double *zinit, const double *hist_init,
+                         double *y_out, double *delta_out, double *est_out)
+{
+    const int n = pb->n;
+    double z[(QMAX + 2) * n], J[n * n], f[n], acor[n], ycur[n], del[n], w[n];
+    double hist[QMAX + 1], xi[QMAX + 2], l[QMAX + 2];
+    int32_t piv[n];
+    memcpy(z, zinit, sizeof(double) * (q + 1) * n);
+    memcpy(hist, hist_init, sizeof(double) * (QMAX + 1));
+    for (int i = 0; i < n; ++i) w[i] = 1.0;
+    for (int step = 0; step < nsteps; ++step) {
+        for (int k = 0; k < q; ++k)
+            for (int j = q; j > k; --j)
+                for (int i = 0; i < n; ++i) z[(j - 1) * n + i] += z[j * n + i];
+        bdf_xi(q + 1, h, hist, xi);
+        orc_bdf_l(q, xi, l);
+        double gamma = h / l[1];
+        for (int i = 0; i < n; ++i) { acor[i] = 0.0; ycur[i] = z[i]; }
+        for (int it = 0; it < 50; ++it) {
+            rhs_r(pb, cell, ycur, f);
+            orc_jac(pb, cell, ycur, f, w, 0, J);
+            for (int i = 0; i < n * n; ++i) J[i] = -gamma * J[i];
+            for (int i = 0; i < n; ++i) J[i * n + i] += 1.0;
+            if (orc_lu_factor(n, J, piv)) return -1;
+            for (int i = 0; i < n; ++i) del[i] = (h * f[i] - z[n + i]) / l[1] - acor[i];
+            orc_lu_solve(n, J, piv, del);
+            double dmax = 0.0, ymax = 0.0;
+            for (int i = 0; i < n; ++i) {
+                acor[i] += del[i]; ycur[i] = z[i] + acor[i];
+                dmax = fmax(dmax, fabs(del[i])); ymax = fmax(ymax, fabs(ycur[i]));
+            }
+            if (dmax <= 1e-15 * ymax || dmax == 0.0) break;
+        }
+        double Cq = 1.0 / (1.0 + l[1] * xi[q]);
+        for (int j = 0; j <= q; ++j)
+            for (int i = 0; i < n; ++i) z[j * n + i] += l[j] * acor[i];
+        for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
+        hist[0] = h;
+        if (step == nsteps - 1) {
+            for (int i = 0; i < n; ++i) {
+                if (delta_out) delta_out[i] = acor[i];
+                if (est_out) est_out[i] = Cq * acor[i];
+            }
+        }
+    }
+    memcpy(y_out, z, sizeof(double) * n);
+    return 0;
+}
