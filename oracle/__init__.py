@@ -75,7 +75,7 @@ def lib():
         L.orc_integrate.restype = ctypes.c_int
         L.orc_num_threads.restype = ctypes.c_int
         L.orc_bdf_fixed.argtypes = [PP, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_int,
-                                    _dp, _dp, _dp, _dp, _dp]
+                                    _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_bdf_fixed.restype = ctypes.c_int
         _lib = L
     return _lib
@@ -216,16 +216,20 @@ def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
 
 
 def bdf_fixed(pb, q, h, nsteps, zinit, hist, cell=0):
+    """Fixed h and q from the Nordsieck array zinit [(q+1), n] and previous
+    step sizes hist; returns (y, Delta, E, z) after the last step."""
     zinit = _f64(zinit)
     hist6 = np.zeros(6)
     hist6[:len(hist)] = hist
     y = np.empty(pb.n)
     dl = np.empty(pb.n)
     est = np.empty(pb.n)
-    rc = lib().orc_bdf_fixed(pb.ref, cell, q, h, nsteps, _d(zinit), _d(hist6), _d(y), _d(dl), _d(est))
+    z = np.empty((q + 1, pb.n))
+    rc = lib().orc_bdf_fixed(pb.ref, cell, q, h, nsteps, _d(zinit), _d(hist6), _d(y),
+                             _d(dl), _d(est), _d(z))
     if rc:
         raise RuntimeError("singular Newton matrix")
-    return y, dl, est
+    return y, dl, est, z
 
 
 def num_threads():

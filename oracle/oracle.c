@@ -522,11 +522,13 @@ EXPORT int orc_num_threads(void)
 /* Fixed step size, fixed order q: nsteps steps of size h from a given
  * Nordsieck array zinit ((q+1) x n) and step history (previous step sizes,
  * 6 entries), each corrector solved by full Newton to rounding level.
- * Returns y at the end, and for the last step the correction Delta and the
- * estimate E = C_q Delta.  Used to pin coefficients, order and estimate. */
+ * Returns y at the end, and for the last step the correction Delta, the
+ * estimate E = C_q Delta and the corrected Nordsieck array.  Used to pin the
+ * coefficients, the order and the error estimate. */
 EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int nsteps,
                          const double *zinit, const double *hist_init,
-                         double *y_out, double *delta_out, double *est_out)
+                         double *y_out, double *delta_out, double *est_out,
+                         double *z_out)
 {
     const int n = pb->n;
     double z[(QMAX + 2) * n], J[n * n], f[n], acor[n], ycur[n], del[n], w[n];
@@ -571,5 +573,6 @@ EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int 
         }
     }
     memcpy(y_out, z, sizeof(double) * n);
+    if (z_out) memcpy(z_out, z, sizeof(double) * (q + 1) * n);
     return 0;
 }
