@@ -1,0 +1,361 @@
+"""Benchmark: cells integrated per outer step per second on one B300.
+
+One step = one outer step dt_CFD (Sec. 2 of arXiv 2405.01713): every cell of
+the workload is advanced from t0 to tout by sunb_integrate, from the same
+seeded initial state (re-copied on the device inside the timed region).
+
+Default workload: the 22-unknown synthetic mechanism, 2**18 cells, dt 1e-6 s,
+rtol 1e-6, atol 1e-10, FP64 right-hand side and error control.  Two forms are
+timed: "plain" (FP64 Newton matrix and LU, one warp per cell, static cell
+assignment) and "chosen" (FP32 Newton matrix and LU, device work queue,
+autotuned lanes-per-cell mapping); ``value`` is the chosen form.
+
+Prints one JSON line (see the repository's benchmark contract).
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "cells/s integrated per outer step at rtol 1e-6, plain FP64 vs mixed/persistent"
+UNIT = "cells/s"
+FP64_PEAK_DERIVED = 148 * 2032e6 * 2 * 2 / 1e12   # TFLOP/s: SMs x max clock x 2 DFMA/clk/SM x 2 flop
+
+
+# --------------------------------------------------------------------- work model
+def rhs_flops(mech):
+    """Algorithmic FP64 operations of one mechanism right-hand side
+    (transcendentals count as one operation each)."""
+    K, M = mech.n_species, mech.n_reactions
+    nnz = 0
+    for k in range(K):
+        for j in range(M):
+            net = int(np.sum(mech.prod[j] == k) - np.sum(mech.react[j] == k))
+            nnz += net != 0
+    per_reaction = 4 + 1 + 7 + 6 + 1          # exponent, exp, kr product, C products, q
+    per_species = 33 + 2 + 6                  # NASA cp/h/s + exp + C, f, energy terms
+    return M * per_reaction + K * per_species + 2 * nnz + 20
+
+
+def jac_extra_flops(mech):
+    """Operations of the analytic Jacobian beyond the shared right-hand side."""
+    K, M, N = mech.n_species, mech.n_reactions, mech.n_vars
+    nnz = 0
+    for k in range(K):
+        for j in range(M):
+            net = int(np.sum(mech.prod[j] == k) - np.sum(mech.react[j] == k))
+            nnz += net != 0
+    return M * 22 + nnz * 14 + 2 * K * K + 2 * K * K + 4 * K * K + 10 * K + N * N
+
+
+def work_model(w, tot):
+    """Algorithmic FP64 flops of one launch from the per-cell counters:
+    f evaluations, Newton-matrix builds (J + LU (2/3)N^3), Newton iterations
+    (solve 2N^2 + 8N vector work) and steps (predict, correct, weights,
+    norms; order 4 taken as typical)."""
+    if w["kind"] == "mechanism":
+        N = w["mech"].n_vars
+        f_rhs = rhs_flops(w["mech"])
+        f_setup = jac_extra_flops(w["mech"]) + (2.0 / 3.0) * N ** 3
+    else:
+        N = 3
+        f_rhs, f_setup = 12, 9 + (2.0 / 3.0) * 27
+    q = 4
+    f_step = (q * (q + 1) / 2) * N + 2 * (q + 1) * N + 3 * N + 8 * N + 120
+    f_iter = 2 * N * N + 8 * N
+    return (tot["nfe"] * f_rhs + tot["nje"] * f_setup + tot["nni"] * f_iter + tot["nst"] * f_step)
+
+
+# --------------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi SM clock and throttle reasons sampled every 200 ms."""
+
+    Q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index=0):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 8:
+                continue
+            try:
+                sm.append(float(p[0]))
+                mx.append(float(p[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, p[4:8]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------- workloads
+def make_workload(name):
+    if name == "mech22":
+        return synth.workloads.mech22()
+    if name == "mech54":
+        return synth.workloads.mech54()
+    if name == "robertson":
+        return synth.workloads.robertson()
+    if name == "mixed":
+        return synth.workloads.mixed()
+    if name == "cosmology":
+        return synth.workloads.cosmology(2 ** 24)
+    raise ValueError(name)
+
+
+FORMS = {
+    "plain": dict(precision=0, lanes_per_cell=32, schedule=1),
+    "chosen": dict(precision=1, lanes_per_cell=0, schedule=0),
+}
+
+
+def flat_inputs(w):
+    if w["kind"] == "mixed":
+        Y = np.concatenate([w["e0"].ravel(), w["y0_mech"].ravel()])
+        P = np.concatenate([w["cosmo_params"].ravel(), w["mech_params"].ravel()])
+        C = w["n_cosmo"] + w["n_mech"]
+    else:
+        Y, P, C = w["y0"].ravel(), w["params"].ravel(), w["n_cells"]
+    return np.ascontiguousarray(Y), np.ascontiguousarray(P), C
+
+
+def make_integrator(w, form):
+    import paper_2405_01713_b300 as sb
+    kw = FORMS[form]
+    prec = kw["precision"] if w["kind"] in ("mechanism", "mixed") else 0
+    return sb.from_workload(w, precision=prec, lanes_per_cell=kw["lanes_per_cell"],
+                            schedule=kw["schedule"])
+
+
+def time_form(w, form, steps, warmup, flush):
+    """Device-resident timing of one form: per step, copy y0 -> y and
+    integrate, bracketed by CUDA events on the integrator's stream; an L2
+    flush (a 512 MiB write) runs between steps outside the events."""
+    import torch
+    Y, P, C = flat_inputs(w)
+    it = make_integrator(w, form)
+    stream = torch.cuda.current_stream()
+    y0 = torch.tensor(Y, device="cuda")
+    y = torch.empty_like(y0)
+    p = torch.tensor(P, device="cuda")
+    it.set_params(p)
+    for _ in range(warmup):
+        y.copy_(y0)
+        it.integrate(y, w["t0"], w["tout"])
+    torch.cuda.synchronize()
+    l0 = it.launch_count
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y.copy_(y0)
+        it.integrate(y, w["t0"], w["tout"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    launches = it.launch_count - l0
+    tot = it.totals()
+    mapping = it.mapping() if w["kind"] in ("mechanism", "mixed") else None
+    it.close()
+    return dict(ms=times, launches=launches, totals=tot, mapping=mapping, C=C)
+
+
+def time_e2e(w, form, steps, warmup):
+    """End to end through sunb_integrate_host: per step the host state (pinned)
+    is copied to the device, integrated and copied back."""
+    import torch
+    Y, P, C = flat_inputs(w)
+    it = make_integrator(w, form)
+    p = torch.tensor(P, device="cuda")
+    it.set_params(p)
+    host = torch.empty(Y.size, dtype=torch.float64, pin_memory=True).numpy()
+    for _ in range(warmup):
+        host[:] = Y
+        it.integrate_host(host, w["t0"], w["tout"])
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(steps):
+        host[:] = Y
+        t0 = time.perf_counter()
+        it.integrate_host(host, w["t0"], w["tout"])
+        ts.append(time.perf_counter() - t0)
+    it.close()
+    ms = 1e3 * statistics.mean(ts)
+    return dict(value=C / (ms / 1e3), unit=UNIT, h2d_bytes_per_step=int(Y.size * 8),
+                d2h_bytes_per_step=int(Y.size * 8), ms_per_step=ms)
+
+
+# --------------------------------------------------------------------- CPU baseline
+def cpu_baseline(w, budget_s=12.0):
+    """The oracle as it stands, on the host's cores, on a bounded sample of
+    the workload (the first n cells; n sized to ~budget_s)."""
+    import oracle
+    nth = oracle.num_threads()
+    if w["kind"] == "mixed":
+        wc = synth.workloads.cosmology(4096)
+        wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
+                  t0=0.0, tout=w["tout"])
+        parts = [(wc, w["n_cosmo"]), (wm, w["n_mech"])]
+    else:
+        parts = [(w, w["n_cells"])]
+    total_s, descr = 0.0, []
+    for ww, Cfull in parts:
+        n = min(Cfull, 2 * nth)
+        while True:
+            cells = np.arange(n)
+            pb = oracle.problem_from_workload(ww, cells=cells)
+            t = time.perf_counter()
+            oracle.integrate(pb, ww["y0"][:n], ww["t0"], ww["tout"], ww.get("rtol", 1e-6),
+                             ww.get("atol", 1e-10), nthreads=nth)
+            dt = time.perf_counter() - t
+            if dt > budget_s / len(parts) / 4 or n >= Cfull:
+                break
+            n = min(Cfull, int(n * max(2.0, (budget_s / len(parts)) / max(dt, 1e-3))))
+        total_s += dt * Cfull / n
+        descr.append(f"first {n} of {Cfull} cells ({dt:.1f} s)")
+    return dict(value=sum(p[1] for p in parts) / total_s, unit=UNIT, cores=nth, kind="oracle",
+                sample="; ".join(descr) + ", extrapolated to the full batch")
+
+
+# --------------------------------------------------------------------- main
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="sunb", choices=["sunb", "reference"])
+    ap.add_argument("--workload", default="mech22",
+                    choices=["mech22", "mech54", "mixed", "robertson", "cosmology"])
+    ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args()
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    w = make_workload(args.workload)
+    workload_name = {"mech22": "mech22: 21 species + T, 84 reactions, 2^18 cells, dt 1e-6 s",
+                     "mech54": "mech54: 53 species + T, 270 reactions, 2^20 cells, dt 1e-6 s",
+                     "mixed": "mixed: 2^24 cosmology cells + 2^16 mech22 cells, dt 1e-6 s",
+                     "robertson": "robertson: 1024 cells, t 0 -> 1e5",
+                     "cosmology": "cosmology: 2^24 cells, dt 1e-6 s"}[args.workload]
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        cb = cpu_baseline(w, budget_s=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
+        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+                "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+                "config": {"workload": workload_name, "rtol": 1e-6, "atol": 1e-10},
+                "cpu_baseline": cb,
+                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    import torch
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+
+    clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
+    res_plain = None
+    if not args.no_plain and w["kind"] in ("mechanism", "mixed"):
+        res_plain = time_form(w, "plain", args.steps, args.warmup, flush)
+    clocks.start()
+    res = time_form(w, "chosen", args.steps, args.warmup, flush)
+    clk = clocks.stop()
+    ms = statistics.mean(res["ms"])
+    if world > 1:
+        import torch.distributed as dist
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * res["C"] / (ms / 1e3)
+
+    # the counters describe the last launch (they are reset by every call)
+    flops = work_model(w if w["kind"] != "mixed" else dict(kind="mechanism", mech=w["mech"]),
+                       res["totals"])
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
+            "frac": achieved / FP64_PEAK_DERIVED, "traffic": None,
+            "peak_source": "derived: 148 SMs x 2032 MHz x 2 DFMA/clk/SM x 2 (FP64 pipe)"}
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": workload_name, "rtol": 1e-6, "atol": 1e-10,
+                       "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
+                       "mapping": res["mapping"][:3] if res["mapping"] else None,
+                       "l2": "flushed between steps (512 MiB write)"},
+            "roofline": roof, "gpu_launches": res["launches"], "clocks": clk,
+            "work": {k: res["totals"][k] for k in ("nst", "nfe", "nje", "nni", "nef", "ncf",
+                                                     "max_nst", "n_failed")}}
+    if res_plain is not None:
+        mp = statistics.mean(res_plain["ms"])
+        line["forms"] = {"plain_fp64": {"value": res_plain["C"] / (mp / 1e3), "ms_per_step": mp,
+                                        "mapping": res_plain["mapping"][:3]},
+                         "chosen": {"value": res["C"] / (ms / 1e3), "ms_per_step": ms,
+                                    "mapping": res["mapping"][:3],
+                                    "autotune_trial_ms": res["mapping"][3]}}
+    if not args.no_e2e:
+        line["e2e"] = time_e2e(w, "chosen", max(1, min(args.steps, 2)), 1)
+    if not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(w)
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,199 @@
+/*
+ * sunb.h -- C ABI of a batched stiff-ODE integrator for NVIDIA B300 (sm_103a).
+ *
+ * It integrates many small, independent ODE systems y_c' = f(t, y_c; p_c),
+ * one per cell, the setting of arXiv 2405.01713 (Balos et al., "SUNDIALS
+ * Time Integrators for Exascale Applications with Many Independent ODE
+ * Systems"): operator splitting (Sec. 1, Sec. 3.1 Eq. chemODE, Sec. 3.2
+ * Eq. nyxODE) leaves one decoupled ODE per cell to be advanced over the
+ * outer step dt_CFD.  Each cell runs a variable-order (1..5), variable-step
+ * BDF method of the CVODE kind (Sec. 2, Eq. 1) with the WRMS error test of
+ * Eq. wrms, the modified Newton iteration and stopping test of
+ * Eq. stop_newton, a dense Jacobian and a pivoted LU (Table 1, approach 2A;
+ * Sec. 4.1.4, 4.1.6).  Unlike the paper's batches, cells do not advance in
+ * lock-step: every cell chooses its own steps and orders.
+ *
+ * Conventions
+ *  - State arrays are cell-contiguous ("CY" order, Sec. 4.1.2): y[c*N + i].
+ *  - Pointers named dev_* are CUDA device pointers owned by the caller; the
+ *    library never frees them.  Pointers named host_* (and the tables of
+ *    sunb_problem) are host memory, read during the call only.
+ *  - All device work is enqueued on the stream given to sunb_create and is
+ *    asynchronous unless stated; the caller must keep device buffers alive
+ *    until the stream has passed the work.
+ *  - Every function returns an int status (sunb_status).  Invalid arguments
+ *    return SUNB_ILL_INPUT before anything is launched; CUDA failures return
+ *    SUNB_CUDA_ERROR.  sunb_last_error() describes the last failure.  No
+ *    function aborts or throws.
+ *  - A context is not thread-safe; use one context per stream.
+ */
+#ifndef SUNB_H
+#define SUNB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct sunb_ctx sunb_ctx;
+
+typedef enum {
+    SUNB_SUCCESS = 0,
+    SUNB_TOO_MUCH_WORK = -1,   /* a cell hit max_steps before tout          */
+    SUNB_ERR_FAILURE = -3,     /* seven error-test failures in one step     */
+    SUNB_CONV_FAILURE = -4,    /* ten Newton failures in one step           */
+    SUNB_H_TOO_SMALL = -5,     /* the step no longer advances t             */
+    SUNB_NONFINITE = -6,       /* f(t0, y0) or y0 not finite                */
+    SUNB_MEM_FAIL = -20,       /* device or host allocation failed          */
+    SUNB_ILL_INPUT = -22,      /* invalid argument                          */
+    SUNB_CUDA_ERROR = -30,     /* a CUDA call failed                        */
+    SUNB_NO_RECORD = -31       /* adjoint asked without a recorded forward  */
+} sunb_status;
+
+typedef enum {
+    SUNB_ROBERTSON = 0,  /* N = 3, params [C,3] = (k1, k2, k3)                     */
+    SUNB_MECHANISM = 1,  /* N = K+1 (Y_1..Y_K, T), params [C,1] = pressure (dyn/cm2) */
+    SUNB_COSMOLOGY = 2,  /* N = 1 (e, with T = e), params [C,2] = (rho, F)          */
+    SUNB_MIXED = 3       /* cosmology cells followed by mechanism cells, one launch */
+} sunb_kind;
+
+typedef enum { SUNB_FP64 = 0, SUNB_MIXED32 = 1 } sunb_precision;
+typedef enum { SUNB_SCHED_QUEUE = 0, SUNB_SCHED_STATIC = 1 } sunb_schedule;
+
+/* Reaction mechanism (Sec. 3.1): K species, M reversible reactions with
+ * modified-Arrhenius forward rates and equilibrium constants from
+ * single-range NASA-7 thermodynamics.  Host arrays, copied at create. */
+typedef struct {
+    int32_t n_species;        /* K, 1..63                                   */
+    int32_t n_reactions;      /* M, 1..4096                                 */
+    const double *W;          /* [K] molecular weights, g/mol               */
+    const double *nasa;       /* [K,7] a1..a7: cp/R = a1+a2T+a3T^2+a4T^3+a5T^4 */
+    const int32_t *react;     /* [M,3] reactant species (repeats allowed), -1 = none */
+    const int32_t *prod;      /* [M,3] product species, -1 = none           */
+    const double *lnA;        /* [M] ln of the pre-exponential factor (cgs, mol) */
+    const double *beta;       /* [M] temperature exponent                   */
+    const double *Ea;         /* [M] activation energy, cal/mol             */
+} sunb_mechanism;
+
+/* Piecewise power-law cooling curve (Sec. 3.2): knots strictly increasing
+ * in ln T; the heating term is gamma_heat * (T/1e4)^-0.7 per unit density. */
+typedef struct {
+    int32_t n_knots;          /* 2..256                                     */
+    const double *lnT;        /* [n_knots]                                  */
+    const double *lnLam;      /* [n_knots] ln Lambda at the knots           */
+    double gamma_heat;
+} sunb_cooling_table;
+
+typedef struct {
+    int32_t kind;             /* sunb_kind                                   */
+    int64_t n_cells;          /* cells (for SUNB_MIXED: mechanism cells)     */
+    int64_t n_cells_cosmo;    /* SUNB_MIXED only: cosmology cells            */
+    int32_t max_order;        /* 1..5 (0 = 5)                                */
+    int32_t max_steps;        /* per cell and call (0 = 100000)              */
+    int32_t precision;        /* sunb_precision: FP32 Newton matrix/LU if MIXED32 */
+    int32_t lanes_per_cell;   /* mechanism cells: 8, 16, 32, or 0 = autotune  */
+    int32_t schedule;         /* sunb_schedule                                */
+    int32_t record_adjoint;   /* reserved, must be 0                          */
+    const sunb_mechanism *mech;        /* SUNB_MECHANISM, SUNB_MIXED */
+    const sunb_cooling_table *table;   /* SUNB_COSMOLOGY, SUNB_MIXED */
+} sunb_problem;
+
+/* Totals over all cells of the last sunb_integrate (the work counters the
+ * paper uses as cost measures, Sec. 4.1.1 and 4.1.5). */
+typedef struct {
+    int64_t nst, nfe, nje, nni, ncf, nef;   /* steps, f evals, Newton-matrix
+                                               builds, Newton iterations,
+                                               Newton failures, error-test failures */
+    int32_t max_nst;          /* largest per-cell step count                 */
+    int32_t worst_status;     /* most negative per-cell status               */
+    int64_t n_failed;         /* cells with a nonzero status                 */
+} sunb_totals;
+
+/* Create a context: validates the problem, copies the tables to the device
+ * and allocates all workspace once (the pooled-memory lesson of Sec. 4.3.1:
+ * nothing is allocated per call).  stream is a cudaStream_t (NULL = legacy
+ * default stream).  On failure *out is NULL. */
+int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out);
+
+/* Relative tolerance and per-component absolute tolerances of Eq. wrms,
+ * w_i = 1/(rtol |y_i^{n-1}| + atol_i).  host_atol has N entries (for
+ * SUNB_MIXED: the N mechanism entries then one cosmology entry); NULL
+ * means atol_scalar for every component.  Default: 1e-6 and 1e-10. */
+int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const double *host_atol);
+
+/* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
+ * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
+ * cells' pressures).  The pointer is kept, not copied: it must stay valid
+ * while integrations that use it are in flight. */
+int sunb_set_params(sunb_ctx *ctx, const double *dev_params);
+
+/* Advance every cell from t0 to tout (one outer step dt_CFD; Sec. 2) in
+ * place in dev_y [C, N].  Each call is a cold start at order 1 and lands
+ * exactly on tout.  dev_status (nullable, int32 [C]) receives per-cell
+ * statuses; a cell that fails keeps its last accepted state.  Asynchronous:
+ * the return value only reports launch problems; see sunb_get_totals. */
+int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t *dev_status);
+
+/* Same from host memory: copies host_y [C, N] to a library buffer,
+ * integrates, copies back, and waits for the stream.  host_status is
+ * nullable.  Returns the most negative per-cell status. */
+int sunb_integrate_host(sunb_ctx *ctx, double *host_y, double t0, double tout, int32_t *host_status);
+
+/* Waits for the stream, then fills *host_totals (nullable) and copies the
+ * per-cell counters to dev_cell_stats (nullable, int32 [C, 8]: nst, nfe,
+ * nje, nni, ncf, nef, last order, status).  Returns the worst status. */
+int sunb_get_totals(sunb_ctx *ctx, sunb_totals *host_totals, int32_t *dev_cell_stats);
+
+/* Evaluate the right-hand side f(y) for n_cells cells (step a5 on its own):
+ * dev_y, dev_f [n_cells, N], cell c uses parameters of cell c. */
+int sunb_rhs(sunb_ctx *ctx, const double *dev_y, double *dev_f, int64_t n_cells);
+
+/* Evaluate the dense Jacobian df/dy (row-major [n_cells, N, N]) of the
+ * mechanism or Robertson right-hand side (step a6 on its own). */
+int sunb_jac(sunb_ctx *ctx, const double *dev_y, double *dev_J, int64_t n_cells);
+
+/* Batched dense LU with row partial pivoting (first row of largest
+ * magnitude) and solve (step a7, Sec. 4.1.6): for each of batch systems,
+ * factor dev_A [batch, n, n] in place (unit-lower L below the diagonal,
+ * U on and above it), write the row exchanges LAPACK-style to dev_piv
+ * [batch, n] (0-based), overwrite dev_b [batch, n] with the solution, and
+ * set dev_info [batch] to 0 or k+1 for a zero pivot in column k.  n <= 64.
+ * Runs on the given stream (a cudaStream_t). */
+int sunb_lu_solve_batched(int32_t n, int64_t batch, double *dev_A, int32_t *dev_piv,
+                          double *dev_b, int32_t *dev_info, void *stream);
+
+/* FP32 version of sunb_lu_solve_batched (the matrix precision of the
+ * mixed form). */
+int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *dev_piv,
+                              float *dev_b, int32_t *dev_info, void *stream);
+
+/* Lanes per mechanism cell chosen by the context (autotuned when asked). */
+int sunb_get_lanes_per_cell(const sunb_ctx *ctx);
+
+/* Mechanism mapping in use: lanes per cell, cells per CTA, CTAs per SM;
+ * trial_ms (nullable, 6 floats) receives the autotuner's trial times for
+ * L = 8, 16, 32 at two CTA sizes each (0 = not run, -1 = duplicate).  With
+ * lanes_per_cell = 0 at create, the first sunb_integrate runs the trials
+ * (synchronously, on a scratch copy of the first cells) and keeps the
+ * fastest mapping for the context's lifetime. */
+int sunb_get_mapping(const sunb_ctx *ctx, int32_t *lanes_per_cell, int32_t *cells_per_cta,
+                     int32_t *ctas_per_sm, float *trial_ms);
+
+/* Number of the library's kernel launches enqueued so far by this context. */
+int64_t sunb_get_launch_count(const sunb_ctx *ctx);
+
+int sunb_destroy(sunb_ctx *ctx);
+
+/* Description of the last failure of ctx (or of a failed create when ctx is
+ * NULL); never NULL. */
+const char *sunb_last_error(const sunb_ctx *ctx);
+
+const char *sunb_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SUNB_H */

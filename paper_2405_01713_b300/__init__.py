@@ -1,0 +1,281 @@
+"""Batched stiff-ODE (BDF) integration on B300: Python binding of libsunb.
+
+Argument marshalling only: every step of the integration runs in the CUDA
+kernels of ``libsunb.so`` (declared in ``include/sunb.h``); PyTorch supplies
+device memory and the stream.  The library must have been built
+(``python -m paper_2405_01713_b300.build``); importing the binding without it
+raises ``ImportError`` -- there is no CPU fallback.
+
+Method: arXiv 2405.01713 (Balos et al.), Sec. 2 -- one variable-order,
+variable-step BDF integration per cell with WRMS error control (Eq. wrms),
+modified Newton (Eq. stop_newton), analytic dense Jacobian and pivoted LU
+(Table 1, approach 2A).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libsunb.so")
+
+ROBERTSON, MECHANISM, COSMOLOGY, MIXED = 0, 1, 2, 3
+FP64, MIXED32 = 0, 1
+SCHED_QUEUE, SCHED_STATIC = 0, 1
+STATUS = {0: "SUCCESS", -1: "TOO_MUCH_WORK", -3: "ERR_FAILURE", -4: "CONV_FAILURE",
+          -5: "H_TOO_SMALL", -6: "NONFINITE", -20: "MEM_FAIL", -22: "ILL_INPUT",
+          -30: "CUDA_ERROR", -31: "NO_RECORD"}
+SUCCESS, TOO_MUCH_WORK, ERR_FAILURE, CONV_FAILURE, H_TOO_SMALL, NONFINITE = 0, -1, -3, -4, -5, -6
+ILL_INPUT, CUDA_ERROR = -22, -30
+STAT_FIELDS = ("nst", "nfe", "nje", "nni", "ncf", "nef", "qlast", "status")
+
+_vp = ctypes.c_void_p
+_dp = ctypes.POINTER(ctypes.c_double)
+_ip = ctypes.POINTER(ctypes.c_int32)
+
+
+class SunbError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"{STATUS.get(code, code)} ({code}): {msg}")
+        self.code = code
+
+
+class _Mechanism(ctypes.Structure):
+    _fields_ = [("n_species", ctypes.c_int32), ("n_reactions", ctypes.c_int32),
+                ("W", _dp), ("nasa", _dp), ("react", _ip), ("prod", _ip),
+                ("lnA", _dp), ("beta", _dp), ("Ea", _dp)]
+
+
+class _Table(ctypes.Structure):
+    _fields_ = [("n_knots", ctypes.c_int32), ("lnT", _dp), ("lnLam", _dp),
+                ("gamma_heat", ctypes.c_double)]
+
+
+class _Problem(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n_cells", ctypes.c_int64),
+                ("n_cells_cosmo", ctypes.c_int64), ("max_order", ctypes.c_int32),
+                ("max_steps", ctypes.c_int32), ("precision", ctypes.c_int32),
+                ("lanes_per_cell", ctypes.c_int32), ("schedule", ctypes.c_int32),
+                ("record_adjoint", ctypes.c_int32),
+                ("mech", ctypes.POINTER(_Mechanism)), ("table", ctypes.POINTER(_Table))]
+
+
+class _Totals(ctypes.Structure):
+    _fields_ = [("nst", ctypes.c_int64), ("nfe", ctypes.c_int64), ("nje", ctypes.c_int64),
+                ("nni", ctypes.c_int64), ("ncf", ctypes.c_int64), ("nef", ctypes.c_int64),
+                ("max_nst", ctypes.c_int32), ("worst_status", ctypes.c_int32),
+                ("n_failed", ctypes.c_int64)]
+
+
+# name -> (restype, argtypes); every symbol declared in include/sunb.h
+SIGNATURES = {
+    "sunb_create": (ctypes.c_int, [ctypes.POINTER(_Problem), _vp, ctypes.POINTER(_vp)]),
+    "sunb_set_tolerances": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp]),
+    "sunb_set_params": (ctypes.c_int, [_vp, _vp]),
+    "sunb_integrate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
+    "sunb_integrate_host": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_double, _ip]),
+    "sunb_get_totals": (ctypes.c_int, [_vp, ctypes.POINTER(_Totals), _vp]),
+    "sunb_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
+    "sunb_jac": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
+    "sunb_lu_solve_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "sunb_lu_solve_batched_f32": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "sunb_get_lanes_per_cell": (ctypes.c_int, [_vp]),
+    "sunb_get_launch_count": (ctypes.c_int64, [_vp]),
+    "sunb_get_mapping": (ctypes.c_int, [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
+    "sunb_destroy": (ctypes.c_int, [_vp]),
+    "sunb_last_error": (ctypes.c_char_p, [_vp]),
+    "sunb_version": (ctypes.c_char_p, []),
+}
+
+_lib = None
+
+
+def lib():
+    """The loaded libsunb.so; raises ImportError if it was not built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libsunb.so is not built; run `python -m paper_2405_01713_b300.build` "
+                              "(the integrator has no CPU fallback)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(L, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ctx=None):
+    if rc != 0:
+        msg = lib().sunb_last_error(ctx).decode()
+        raise SunbError(rc, msg)
+    return rc
+
+
+def _stream_handle(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _cont(a, dtype):
+    return np.ascontiguousarray(a, dtype=dtype)
+
+
+class Integrator:
+    """One context of the C ABI: a batch of cells of one kind (or the mixed
+    cosmology + mechanism batch), integrated on one CUDA stream."""
+
+    def __init__(self, kind, n_cells, mech=None, table=None, n_cells_cosmo=0,
+                 max_order=5, max_steps=100000, precision=FP64, lanes_per_cell=0,
+                 schedule=SCHED_QUEUE, stream=None):
+        self._keep = []
+        p = _Problem()
+        p.kind, p.n_cells, p.n_cells_cosmo = kind, n_cells, n_cells_cosmo
+        p.max_order, p.max_steps, p.precision = max_order, max_steps, precision
+        p.lanes_per_cell, p.schedule, p.record_adjoint = lanes_per_cell, schedule, 0
+        if mech is not None:
+            arrs = dict(W=_cont(mech.W, np.float64), nasa=_cont(mech.nasa, np.float64),
+                        react=_cont(mech.react, np.int32), prod=_cont(mech.prod, np.int32),
+                        lnA=_cont(mech.lnA, np.float64), beta=_cont(mech.beta, np.float64),
+                        Ea=_cont(mech.Ea, np.float64))
+            self._keep.append(arrs)
+            m = _Mechanism(mech.n_species, mech.n_reactions,
+                           *[arrs[k].ctypes.data_as(_ip if arrs[k].dtype == np.int32 else _dp)
+                             for k in ("W", "nasa", "react", "prod", "lnA", "beta", "Ea")])
+            self._keep.append(m)
+            p.mech = ctypes.pointer(m)
+        if table is not None:
+            lnT, lnLam = _cont(table.lnT, np.float64), _cont(table.lnLam, np.float64)
+            self._keep += [lnT, lnLam]
+            t = _Table(len(lnT), lnT.ctypes.data_as(_dp), lnLam.ctypes.data_as(_dp), table.gamma_heat)
+            self._keep.append(t)
+            p.table = ctypes.pointer(t)
+        self.kind, self.n_cells, self.n_cells_cosmo = kind, n_cells, n_cells_cosmo
+        self.n_vars = {ROBERTSON: 3, COSMOLOGY: 1}.get(kind, mech.n_vars if mech is not None else 0)
+        self._stream = stream
+        ctx = ctypes.c_void_p()
+        rc = lib().sunb_create(ctypes.byref(p), _stream_handle(stream), ctypes.byref(ctx))
+        _check(rc, None)
+        self.ctx = ctx
+        self._params = None
+
+    # -- setup
+    def set_tolerances(self, rtol, atol):
+        atol = np.asarray(atol, dtype=np.float64)
+        if atol.ndim == 0:
+            _check(lib().sunb_set_tolerances(self.ctx, rtol, float(atol), None), self.ctx)
+        else:
+            a = _cont(atol, np.float64)
+            _check(lib().sunb_set_tolerances(self.ctx, rtol, 0.0, a.ctypes.data_as(_dp)), self.ctx)
+
+    def set_params(self, params):
+        """params: float64 CUDA tensor in the kind's layout (kept alive here)."""
+        self._params = params
+        _check(lib().sunb_set_params(self.ctx, _ptr(params)), self.ctx)
+
+    # -- integration
+    def integrate(self, y, t0, tout, status=None):
+        """In-place advance of the float64 CUDA tensor y from t0 to tout."""
+        _check(lib().sunb_integrate(self.ctx, _ptr(y), t0, tout, _ptr(status)), self.ctx)
+
+    def integrate_host(self, y, t0, tout, status=None):
+        """Same for a float64 numpy array in host memory (copied in and out);
+        returns the worst per-cell status."""
+        assert y.dtype == np.float64 and y.flags["C_CONTIGUOUS"]
+        st = status.ctypes.data_as(_ip) if status is not None else None
+        rc = lib().sunb_integrate_host(self.ctx, y.ctypes.data_as(_dp), t0, tout, st)
+        if rc < -6:
+            _check(rc, self.ctx)
+        return rc
+
+    def totals(self, cell_stats=None):
+        t = _Totals()
+        rc = lib().sunb_get_totals(self.ctx, ctypes.byref(t), _ptr(cell_stats))
+        if rc < -6:
+            _check(rc, self.ctx)
+        return {f: getattr(t, f) for f, _ in _Totals._fields_}
+
+    def cell_stats(self):
+        import torch
+        out = torch.empty((self.n_cells + self.n_cells_cosmo, 8), dtype=torch.int32, device="cuda")
+        self.totals(out)
+        return out
+
+    # -- single steps of the path
+    def rhs(self, y, out=None):
+        import torch
+        out = torch.empty_like(y) if out is None else out
+        _check(lib().sunb_rhs(self.ctx, _ptr(y), _ptr(out), y.shape[0]), self.ctx)
+        return out
+
+    def jac(self, y, out=None):
+        import torch
+        n = y.shape[1]
+        out = torch.empty((y.shape[0], n, n), dtype=torch.float64, device=y.device) if out is None else out
+        _check(lib().sunb_jac(self.ctx, _ptr(y), _ptr(out), y.shape[0]), self.ctx)
+        return out
+
+    @property
+    def lanes_per_cell(self):
+        return lib().sunb_get_lanes_per_cell(self.ctx)
+
+    def mapping(self):
+        """(lanes per cell, cells per CTA, CTAs per SM, autotuner trial ms)."""
+        a, b, c = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        t = (ctypes.c_float * 6)()
+        _check(lib().sunb_get_mapping(self.ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c), t),
+               self.ctx)
+        return a.value, b.value, c.value, list(t)
+
+    @property
+    def launch_count(self):
+        return lib().sunb_get_launch_count(self.ctx)
+
+    def close(self):
+        if getattr(self, "ctx", None):
+            lib().sunb_destroy(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def lu_solve_batched(A, b, stream=None):
+    """Batched pivoted LU and solve on the GPU: A [B, n, n], b [B, n] CUDA
+    tensors (float64 or float32), modified in place into the factors and the
+    solution.  Returns (piv, info) int32 tensors."""
+    import torch
+    B, n = A.shape[0], A.shape[1]
+    piv = torch.empty((B, n), dtype=torch.int32, device=A.device)
+    info = torch.empty((B,), dtype=torch.int32, device=A.device)
+    fn = lib().sunb_lu_solve_batched if A.dtype == torch.float64 else lib().sunb_lu_solve_batched_f32
+    _check(fn(n, B, _ptr(A), _ptr(piv), _ptr(b), _ptr(info), _stream_handle(stream)))
+    return piv, info
+
+
+def from_workload(w, precision=FP64, lanes_per_cell=0, schedule=SCHED_QUEUE, max_steps=100000,
+                  stream=None):
+    """Integrator for a workload dict of ``synth.workloads`` (tolerances set)."""
+    kind = {"robertson": ROBERTSON, "mechanism": MECHANISM, "cosmology": COSMOLOGY,
+            "mixed": MIXED}[w["kind"]]
+    if kind == MIXED:
+        it = Integrator(MIXED, w["n_mech"], mech=w["mech"], table=w["table"],
+                        n_cells_cosmo=w["n_cosmo"], precision=precision,
+                        lanes_per_cell=lanes_per_cell, schedule=schedule,
+                        max_steps=max_steps, stream=stream)
+        it.set_tolerances(w["rtol"], np.full(w["mech"].n_vars + 1, w["atol"]))
+    else:
+        it = Integrator(kind, w["n_cells"], mech=w.get("mech"), table=w.get("table"),
+                        precision=precision, lanes_per_cell=lanes_per_cell,
+                        schedule=schedule, max_steps=max_steps, stream=stream)
+        it.set_tolerances(w["rtol"], w["atol"])
+    return it

@@ -1,0 +1,540 @@
+// Group-of-lanes-per-cell backend for reaction mechanisms (N = K + 1 up to
+// 64 unknowns): L lanes (8, 16 or 32) serve one cell, several cells share a
+// warp when L < 32.  The Nordsieck history, the Newton vectors, the Newton
+// matrix and the right-hand-side scratch of each cell live in shared memory
+// ("CY" order, Sec. 4.1.2: all components of a cell contiguous, so the
+// per-cell Jacobian is a dense block); the mechanism tables are staged once
+// per CTA.  Group reductions are butterfly shuffles within the L lanes, so
+// every result is deterministic.
+//
+// Right-hand side: the chemical source term R of Eq. chemODE (Sec. 3.1) for
+// a constant-pressure adiabatic reactor, y = (Y_1..Y_K, T):
+//   rho = P/(Ru T sum_k Y_k/W_k),  C_k = rho Y_k / W_k,
+//   kf_j = exp(ln A_j + b_j ln T - (Ea_j/Rc)/T),
+//   kr_j = kf_j / Kc_j,  Kc_j = exp(-dG_j/RT) (P_atm/(Ru T))^dnu_j,
+//   q_j = kf_j prod_reac C - kr_j prod_prod C,  wdot_k = sum_j nu_kj q_j,
+//   dY_k/dt = W_k wdot_k / rho,  dT/dt = -T sum_k (h/RT)_k wdot_k / (rho sum_k Y_k (cp/R)_k / W_k).
+// exp(-dG/RT) is formed as a product of per-species factors exp(+-g_k),
+// g_k = (h/RT)_k - (s/R)_k, which needs K exponentials instead of M.
+//
+// Analytic Jacobian (Table 1, "Analytical"; the paper's Sec. 4.1.4 finds it
+// faster than difference quotients).  With Jc = d wdot / d C at fixed T,
+// u = Jc C, Wbar/rho = Ru T / P:
+//   J_kl = (W_k/W_l) (Jc_kl + (Ru T/P)(wdot_k - u_k))
+//   J_kT = (W_k/rho) (dwdot_k/dT|_C + (wdot_k - u_k)/T)
+//   J_Tl = -(1/(W_l cpm)) (T (S_l - (Ru T/P) U) + f_T ((cp/R)_l - cpm Wbar))
+//   J_TT = -(sum_k (cp/R)_k wdot_k + T sum_k (h/RT)_k (dwdot_k/dT|_C - u_k/T)) / (rho cpm)
+//          - f_T (-1/T + sum_k Y_k (dcp/R/dT)_k / W_k / cpm)
+// with S_l = sum_k (h/RT)_k Jc_kl, U = sum_k (h/RT)_k u_k, cpm = sum_k Y_k (cp/R)_k/W_k.
+// The matrix is built pre-multiplied by gamma, so M = I - gamma J directly,
+// in precision MT (double, or float for the mixed form).
+#pragma once
+#include "sunb_common.cuh"
+
+namespace sunb {
+
+// Byte offsets of the mechanism tables inside the staged blob.
+struct MechTabOffsets {
+    int K, M, N, nnz;
+    int invW, W, cpc, hc, sc, dcp, rpar, atol, inc_nu;   // double arrays
+    int ridx, inc_ptr, inc_j;                            // 32-bit arrays
+    int bytes;                                           // blob size (multiple of 16)
+};
+
+// Per-cell shared-memory layout (byte offsets from the cell's base).
+struct CellLayout {
+    int NP;            // padded vector length
+    int vec, mat, perm, xs, sp, rq, dq, bytes;   // xs holds 2N MT (solve scratch, reciprocal pivots)
+};
+
+struct MechTab {
+    int K, M, N;
+    const double *invW, *W, *cpc, *hc, *sc, *dcp, *rpar, *atol, *inc_nu;
+    const uint32_t *ridx;
+    const int32_t *inc_ptr, *inc_j;
+};
+
+__device__ __forceinline__ MechTab mech_tab_at(const unsigned char *base, const MechTabOffsets &o)
+{
+    MechTab t;
+    t.K = o.K; t.M = o.M; t.N = o.N;
+    t.invW = reinterpret_cast<const double *>(base + o.invW);
+    t.W = reinterpret_cast<const double *>(base + o.W);
+    t.cpc = reinterpret_cast<const double *>(base + o.cpc);
+    t.hc = reinterpret_cast<const double *>(base + o.hc);
+    t.sc = reinterpret_cast<const double *>(base + o.sc);
+    t.dcp = reinterpret_cast<const double *>(base + o.dcp);
+    t.rpar = reinterpret_cast<const double *>(base + o.rpar);
+    t.atol = reinterpret_cast<const double *>(base + o.atol);
+    t.inc_nu = reinterpret_cast<const double *>(base + o.inc_nu);
+    t.ridx = reinterpret_cast<const uint32_t *>(base + o.ridx);
+    t.inc_ptr = reinterpret_cast<const int32_t *>(base + o.inc_ptr);
+    t.inc_j = reinterpret_cast<const int32_t *>(base + o.inc_j);
+    return t;
+}
+
+template <int L>
+struct Grp {
+    int lane;
+    unsigned mask;
+    __device__ __forceinline__ double sum(double v) const
+    {
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+        return v;
+    }
+    __device__ __forceinline__ void sync() const { __syncwarp(mask); }
+};
+
+template <typename MT> __device__ __forceinline__ MT mt_rcp(MT x);
+template <> __device__ __forceinline__ double mt_rcp<double>(double x) { return __drcp_rn(x); }
+template <> __device__ __forceinline__ float mt_rcp<float>(float x) { return __frcp_rn(x); }
+
+
+// ---------------- dense LU with row partial pivoting (Sec. 4.1.4, 4.1.6) ----
+// L lanes factor one N x N row-major matrix in place: unit-lower multipliers
+// below the diagonal, U on and above it.  Pivot = first row of largest
+// magnitude (ties to the lower index).  perm[i] is the original row of
+// factored row i; piv (optional) receives the LAPACK-style exchange sequence;
+// dinv[k] = 1/U_kk.  The rank-1 updates spread the (N-k-1)^2 entries over
+// all L lanes.  Returns 1, or 0 if a pivot is zero or not finite.
+template <int L, typename MT>
+__device__ int lu_factor(const Grp<L> &g, MT *mat, int N, int32_t *perm, MT *dinv, int32_t *piv)
+{
+    int ok = 1;
+    for (int i = g.lane; i < N; i += L) perm[i] = i;
+    g.sync();
+    for (int k = 0; k < N; ++k) {
+        MT best = (MT)-1;
+        int bi = N;
+        for (int i = k + g.lane; i < N; i += L) {
+            const MT a = fabs(mat[i * N + k]);
+            if (a > best) { best = a; bi = i; }
+        }
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) {
+            const MT ob = __shfl_xor_sync(g.mask, best, o);
+            const int oi = __shfl_xor_sync(g.mask, bi, o);
+            if (ob > best || (ob == best && oi < bi)) { best = ob; bi = oi; }
+        }
+        ok = ok && (best > (MT)0) && (best <= (MT)3.0e38);
+        const int p = (bi < N) ? bi : k;
+        if (p != k) {
+            for (int j = g.lane; j < N; j += L) {
+                const MT t = mat[k * N + j];
+                mat[k * N + j] = mat[p * N + j];
+                mat[p * N + j] = t;
+            }
+        }
+        if (g.lane == 0) {
+            if (p != k) { const int t = perm[k]; perm[k] = perm[p]; perm[p] = t; }
+            if (piv) piv[k] = p;
+        }
+        g.sync();
+        const MT ip = mt_rcp<MT>(mat[k * N + k]);
+        for (int i = k + 1 + g.lane; i < N; i += L) mat[i * N + k] *= ip;
+        if (g.lane == 0) dinv[k] = ip;
+        g.sync();
+        const int m = N - k - 1;
+        if (m > 0) {
+            const int total = m * m;
+            const int di = L / m, dj = L % m;
+            int ii = g.lane / m, jj = g.lane % m;
+            for (int e = g.lane; e < total; e += L) {
+                MT *r = mat + (k + 1 + ii) * N;
+                r[k + 1 + jj] -= r[k] * mat[k * N + k + 1 + jj];
+                ii += di; jj += dj;
+                if (jj >= m) { jj -= m; ++ii; }
+            }
+        }
+        g.sync();
+    }
+    return ok;
+}
+
+// Solve with the factors of lu_factor: b (length N, type BT) is overwritten
+// by the solution; the arithmetic runs in MT with scratch xs.
+template <int L, typename MT, typename BT>
+__device__ void lu_solve(const Grp<L> &g, const MT *mat, int N, const int32_t *perm,
+                         const MT *dinv, MT *xs, BT *b)
+{
+    for (int i = g.lane; i < N; i += L) xs[i] = (MT)b[perm[i]];
+    g.sync();
+    for (int k = 0; k < N - 1; ++k) {
+        const MT xk = xs[k];
+        for (int i = k + 1 + g.lane; i < N; i += L) xs[i] -= mat[i * N + k] * xk;
+        g.sync();
+    }
+    for (int k = N - 1; k >= 0; --k) {
+        const MT xk = xs[k] * dinv[k];
+        for (int i = g.lane; i < k; i += L) xs[i] -= mat[i * N + k] * xk;
+        g.sync();
+        if (g.lane == 0) xs[k] = xk;
+        g.sync();
+    }
+    for (int i = g.lane; i < N; i += L) b[i] = (BT)xs[i];
+    g.sync();
+}
+
+template <int L, typename MT>
+struct GroupCell {
+    Grp<L> g;
+    MechTab tb;
+    int N, K, M, NP;
+    double invN, P, invP;
+    double *vec;          // [NVEC][NP]
+    MT *mat;              // [N][N], row-major
+    int32_t *perm;        // [N] row permutation of the factorisation
+    MT *xs;               // [N] solve scratch
+    MT *dinv;             // [N] reciprocal pivots
+    double *C, *eg, *egi, *hRT, *cpR, *wdot, *u, *wT;   // species scratch ([K+1] for the first three)
+    double *q, *dq, *dqdT;                              // [M], [6M], [M]
+    double *yg;
+
+    __device__ __forceinline__ double *V(int s) const { return vec + s * NP; }
+
+    __device__ void bind(unsigned char *base, const CellLayout &lay)
+    {
+        NP = lay.NP;
+        vec = reinterpret_cast<double *>(base + lay.vec);
+        mat = reinterpret_cast<MT *>(base + lay.mat);
+        perm = reinterpret_cast<int32_t *>(base + lay.perm);
+        xs = reinterpret_cast<MT *>(base + lay.xs);
+        dinv = xs + N;
+        double *sp = reinterpret_cast<double *>(base + lay.sp);
+        C = sp; eg = C + (K + 1); egi = eg + (K + 1); hRT = egi + (K + 1);
+        cpR = hRT + (K + 1); wdot = cpR + K; u = wdot + K; wT = u + K;
+        q = reinterpret_cast<double *>(base + lay.rq);
+        dq = reinterpret_cast<double *>(base + lay.dq);
+        dqdT = dq + 6 * M;
+        if (g.lane == 0) { C[K] = 1.0; eg[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; }
+        g.sync();
+    }
+
+    // ---------------- vector operations (lane-strided over N) ----------------
+    __device__ __forceinline__ void load_y(int s)
+    {
+        double *d = V(s);
+        for (int i = g.lane; i < N; i += L) d[i] = yg[i];
+        g.sync();
+    }
+    __device__ __forceinline__ void store_y(int s)
+    {
+        const double *d = V(s);
+        for (int i = g.lane; i < N; i += L) yg[i] = d[i];
+    }
+    __device__ __forceinline__ bool all_finite(int s) const
+    {
+        const double *d = V(s);
+        int bad = 0;
+        for (int i = g.lane; i < N; i += L) bad |= !(fabs(d[i]) <= 1.7e308);
+        return __all_sync(g.mask, bad == 0);
+    }
+    __device__ __forceinline__ void set_weights(int s, double rtol)
+    {
+        const double *y = V(s);
+        double *w = V(V_W);
+        for (int i = g.lane; i < N; i += L) w[i] = rcp(rtol * fabs(y[i]) + tb.atol[i]);
+        g.sync();
+    }
+    __device__ __forceinline__ double wrms2(int s) const
+    {
+        const double *a = V(s), *w = V(V_W);
+        double acc = 0.0;
+        for (int i = g.lane; i < N; i += L) { const double t = a[i] * w[i]; acc += t * t; }
+        return g.sum(acc) * invN;
+    }
+    __device__ __forceinline__ double wrms2_lin(double ca, int sa, double cb, int sb) const
+    {
+        const double *a = V(sa), *b = V(sb), *w = V(V_W);
+        double acc = 0.0;
+        for (int i = g.lane; i < N; i += L) {
+            const double t = (ca * a[i] + cb * b[i]) * w[i];
+            acc += t * t;
+        }
+        return g.sum(acc) * invN;
+    }
+    __device__ __forceinline__ void axpby(int o, double ca, int sa, double cb, int sb)
+    {
+        double *d = V(o);
+        const double *a = V(sa), *b = V(sb);
+        for (int i = g.lane; i < N; i += L) d[i] = ca * a[i] + cb * b[i];
+        g.sync();
+    }
+    __device__ __forceinline__ void scale(int o, double ca, int sa)
+    {
+        double *d = V(o);
+        const double *a = V(sa);
+        for (int i = g.lane; i < N; i += L) d[i] = ca * a[i];
+        g.sync();
+    }
+    // Each lane owns the same elements in every column, so the Nordsieck
+    // updates need no synchronisation between columns.
+    __device__ __forceinline__ void predict(int q)
+    {
+        for (int i = g.lane; i < N; i += L) {
+            double z[QMAX + 1];
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) z[j] = (j <= q) ? vec[j * NP + i] : 0.0;
+#pragma unroll
+            for (int k = 0; k < QMAX; ++k)
+#pragma unroll
+                for (int j = QMAX; j >= 1; --j)
+                    if (k < q && j > k && j <= q) z[j - 1] += z[j];
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) if (j <= q) vec[j * NP + i] = z[j];
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void unpredict(int q)
+    {
+        for (int i = g.lane; i < N; i += L) {
+            double z[QMAX + 1];
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) z[j] = (j <= q) ? vec[j * NP + i] : 0.0;
+#pragma unroll
+            for (int k = QMAX - 1; k >= 0; --k)
+#pragma unroll
+                for (int j = 1; j <= QMAX; ++j)
+                    if (k < q && j > k && j <= q) z[j - 1] -= z[j];
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) if (j <= q) vec[j * NP + i] = z[j];
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void rescale(int q, double eta)
+    {
+        double f[QMAX + 1];
+        f[0] = 1.0;
+#pragma unroll
+        for (int j = 1; j <= QMAX; ++j) f[j] = f[j - 1] * eta;
+        for (int i = g.lane; i < N; i += L) {
+#pragma unroll
+            for (int j = 1; j <= QMAX; ++j) if (j <= q) vec[j * NP + i] *= f[j];
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void correct(int q, const double *l)
+    {
+        const double *ac = V(V_ACOR);
+        for (int i = g.lane; i < N; i += L) {
+            const double a = ac[i];
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j) if (j <= q) vec[j * NP + i] += l[j] * a;
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void order_increase(int q, const double *l, double inv_xi)
+    {
+        const double *ac = V(V_ACOR);
+        for (int i = g.lane; i < N; i += L) {
+            const double a = ac[i];
+            vec[(q + 1) * NP + i] = 0.0;
+#pragma unroll
+            for (int j = 1; j <= QMAX; ++j)
+                if (j <= q + 1) vec[j * NP + i] += l[j - 1] * inv_xi * a;
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void order_decrease(int q, const double *e)
+    {
+        for (int i = g.lane; i < N; i += L) {
+            const double zq = vec[q * NP + i];
+#pragma unroll
+            for (int j = 1; j < QMAX; ++j) if (j < q) vec[j * NP + i] -= e[j - 1] * zq;
+            vec[q * NP + i] = 0.0;
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void restart(double h)
+    {
+        const double *f = V(V_F);
+        for (int i = g.lane; i < N; i += L) {
+            vec[NP + i] = h * f[i];
+#pragma unroll
+            for (int j = 2; j <= QMAX; ++j) vec[j * NP + i] = 0.0;
+        }
+        g.sync();
+    }
+    __device__ __forceinline__ void newton_init()
+    {
+        double *ac = V(V_ACOR), *y = V(V_Y);
+        const double *z0 = V(V_Z0);
+        for (int i = g.lane; i < N; i += L) { ac[i] = 0.0; y[i] = z0[i]; }
+        g.sync();
+    }
+    __device__ __forceinline__ void newton_residual(double h, double il1)
+    {
+        double *d = V(V_DEL);
+        const double *f = V(V_F), *z1 = V(V_Z1), *ac = V(V_ACOR);
+        for (int i = g.lane; i < N; i += L) d[i] = (h * f[i] - z1[i]) * il1 - ac[i];
+        g.sync();
+    }
+    __device__ __forceinline__ double newton_update(double c)
+    {
+        double *d = V(V_DEL), *ac = V(V_ACOR), *y = V(V_Y);
+        const double *z0 = V(V_Z0), *w = V(V_W);
+        double acc = 0.0;
+        for (int i = g.lane; i < N; i += L) {
+            const double di = d[i] * c;
+            const double a = ac[i] + di;
+            ac[i] = a;
+            y[i] = z0[i] + a;
+            const double t = di * w[i];
+            acc += t * t;
+        }
+        acc = g.sum(acc) * invN;
+        g.sync();
+        return acc;
+    }
+
+    // ---------------- right-hand side (+ Newton matrix) ----------------
+    template <bool JAC>
+    __device__ int eval(int sin, int sout, double gamma, bool add_identity = true)
+    {
+        const double *y = V(sin);
+        double *f = V(sout);
+        const double T = y[K];
+        const double lnT = log(T), invT = rcp(T);
+        double s = 0.0;
+        for (int k = g.lane; k < K; k += L) s += y[k] * tb.invW[k];
+        s = g.sum(s);
+        const double rts = RU * T * s;
+        const double rho = P * rcp(rts);
+        const double rrho = rts * invP;
+        for (int k = g.lane; k < K; k += L) {
+            const double *a = tb.cpc + 5 * k, *hh = tb.hc + 6 * k, *ss = tb.sc + 6 * k;
+            const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+            const double hrt = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
+            const double sr = ss[0] * lnT + T * (ss[1] + T * (ss[2] + T * (ss[3] + T * ss[4]))) + ss[5];
+            const double e = exp(hrt - sr);
+            C[k] = rho * y[k] * tb.invW[k];
+            eg[k] = e;
+            egi[k] = rcp(e);
+            hRT[k] = hrt;
+            cpR[k] = cp;
+        }
+        g.sync();
+        const double rtp = RU * T * (1.0 / PATM), irtp = rcp(rtp);
+        const double pw[5] = {irtp * irtp, irtp, 1.0, rtp, rtp * rtp};
+        for (int j = g.lane; j < M; j += L) {
+            const uint32_t a = tb.ridx[2 * j], b = tb.ridx[2 * j + 1];
+            const int r0 = a & 0xff, r1 = (a >> 8) & 0xff, r2 = (a >> 16) & 0xff, p0 = a >> 24;
+            const int p1 = b & 0xff, p2 = (b >> 8) & 0xff, dnu = (int)((b >> 16) & 0xff) - 8;
+            const double *rp = tb.rpar + 3 * j;
+            const double kf = exp(rp[0] + rp[1] * lnT - rp[2] * invT);
+            const double kr = kf * (egi[r0] * egi[r1] * egi[r2]) * (eg[p0] * eg[p1] * eg[p2]) * pw[dnu + 2];
+            const double c0 = C[r0], c1 = C[r1], c2 = C[r2];
+            const double d0 = C[p0], d1 = C[p1], d2 = C[p2];
+            const double fwd = kf * (c0 * c1 * c2), rev = kr * (d0 * d1 * d2);
+            q[j] = fwd - rev;
+            if (JAC) {
+                double *dj = dq + 6 * j;
+                const double gkf = gamma * kf, gkr = gamma * kr;
+                dj[0] = gkf * (c1 * c2);
+                dj[1] = gkf * (c0 * c2);
+                dj[2] = gkf * (c0 * c1);
+                dj[3] = -gkr * (d1 * d2);
+                dj[4] = -gkr * (d0 * d2);
+                dj[5] = -gkr * (d0 * d1);
+                const double af = rp[1] + rp[2] * invT;
+                const double dH = (hRT[p0] + hRT[p1] + hRT[p2]) - (hRT[r0] + hRT[r1] + hRT[r2]);
+                dqdT[j] = invT * (af * fwd - (af - dH + (double)dnu) * rev);
+            }
+        }
+        g.sync();
+        double hw = 0.0, cpm = 0.0;
+        for (int k = g.lane; k < K; k += L) {
+            double wd = 0.0;
+            const int e1 = tb.inc_ptr[k + 1];
+            for (int e = tb.inc_ptr[k]; e < e1; ++e) wd += tb.inc_nu[e] * q[tb.inc_j[e]];
+            f[k] = wd * tb.W[k] * rrho;
+            hw += hRT[k] * wd;
+            cpm += y[k] * cpR[k] * tb.invW[k];
+            if (JAC) wdot[k] = wd;
+        }
+        hw = g.sum(hw);
+        cpm = g.sum(cpm);
+        const double fT = -T * hw * rcp(rho * cpm);
+        if (g.lane == 0) f[K] = fT;
+        g.sync();
+        if (!JAC) return 1;
+
+        // ---- Newton matrix M = I - gamma J (gamma folded into dq, dqdT) ----
+        // rows k < K of gamma*Jc, and gamma * dwdot/dT, gamma * u
+        for (int k = g.lane; k < K; k += L) {
+            MT *row = mat + k * N;
+            for (int m = 0; m < N; ++m) row[m] = (MT)0;
+            double wt = 0.0;
+            const int e1 = tb.inc_ptr[k + 1];
+            for (int e = tb.inc_ptr[k]; e < e1; ++e) {
+                const int j = tb.inc_j[e];
+                const double nu = tb.inc_nu[e];
+                const uint32_t a = tb.ridx[2 * j], b = tb.ridx[2 * j + 1];
+                const double *dj = dq + 6 * j;
+                wt += nu * dqdT[j];
+                row[a & 0xff] += (MT)(nu * dj[0]);
+                row[(a >> 8) & 0xff] += (MT)(nu * dj[1]);
+                row[(a >> 16) & 0xff] += (MT)(nu * dj[2]);
+                row[a >> 24] += (MT)(nu * dj[3]);
+                row[b & 0xff] += (MT)(nu * dj[4]);
+                row[(b >> 8) & 0xff] += (MT)(nu * dj[5]);
+            }
+            MT uk = (MT)0;
+            for (int m = 0; m < K; ++m) uk += row[m] * (MT)C[m];
+            wT[k] = gamma * wt;
+            u[k] = (double)uk;
+        }
+        g.sync();
+        // scalars of the temperature row
+        double sU = 0.0, sA1 = 0.0, sA2 = 0.0, sA3 = 0.0;
+        for (int k = g.lane; k < K; k += L) {
+            sU += hRT[k] * u[k];
+            sA1 += cpR[k] * wdot[k];
+            sA2 += hRT[k] * (wT[k] - u[k] * invT);
+            const double *dc = tb.dcp + 4 * k;
+            sA3 += y[k] * (dc[0] + T * (dc[1] + T * (dc[2] + T * dc[3]))) * tb.invW[k];
+        }
+        sU = g.sum(sU); sA1 = g.sum(sA1); sA2 = g.sum(sA2); sA3 = g.sum(sA3);
+        const double Wbar = rcp(s);
+        const double icpm = rcp(cpm);
+        const double rtP = RU * T * invP;               // Wbar / rho
+        // temperature row (from the unscaled-by-W rows of gamma*Jc)
+        for (int l = g.lane; l < K; l += L) {
+            MT Sl = (MT)0;
+            for (int k = 0; k < K; ++k) Sl += (MT)hRT[k] * mat[k * N + l];
+            const double gJ = -(tb.invW[l] * icpm) *
+                              (T * ((double)Sl - rtP * sU) + gamma * fT * (cpR[l] - cpm * Wbar));
+            xs[l] = (MT)gJ;   // staged: row K is written after the k-rows are done
+        }
+        const double gJTT = -(gamma * sA1 + T * sA2) * rcp(rho * cpm) - gamma * fT * (-invT + sA3 * icpm);
+        g.sync();
+        // species rows: gamma*J_kl = (W_k/W_l)(gamma Jc_kl + (Ru T/P) gamma (wdot_k - u_k)), then M = I - gamma J
+        for (int k = g.lane; k < K; k += L) {
+            MT *row = mat + k * N;
+            const double ck = rtP * (gamma * wdot[k] - u[k]);
+            const double Wk = tb.W[k];
+            for (int l = 0; l < K; ++l) {
+                const MT gJ = (MT)(Wk * tb.invW[l]) * (row[l] + (MT)ck);
+                row[l] = ((l == k && add_identity) ? (MT)1 : (MT)0) - gJ;
+            }
+            row[K] = (MT)(-(Wk * rrho) * (wT[k] + (gamma * wdot[k] - u[k]) * invT));
+        }
+        for (int l = g.lane; l < K; l += L) mat[K * N + l] = -xs[l];
+        if (g.lane == 0) mat[K * N + K] = (MT)((add_identity ? 1.0 : 0.0) - gJTT);
+        g.sync();
+        return 1;
+    }
+
+    __device__ __forceinline__ void rhs(int a, int b) { eval<false>(a, b, 0.0); }
+    __device__ __forceinline__ int rhs_setup(int a, int b, double gamma)
+    {
+        eval<true>(a, b, gamma);
+        return factor();
+    }
+
+    __device__ int factor() { return lu_factor<L, MT>(g, mat, N, perm, dinv, nullptr); }
+    __device__ void solve(int sb) { lu_solve<L, MT>(g, mat, N, perm, dinv, xs, V(sb)); }
+};
+
+}  // namespace sunb

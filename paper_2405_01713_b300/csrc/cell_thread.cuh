@@ -1,0 +1,333 @@
+// Thread-per-cell backend for very small systems (N <= 3): Robertson
+// kinetics and the one-unknown heating-cooling cells.  All vectors, the
+// Newton matrix and its pivots live in registers (every loop is unrolled at
+// compile time; runtime indices select through predicates).
+#pragma once
+#include "sunb_common.cuh"
+
+namespace sunb {
+
+// Robertson kinetics: y1' = -k1 y1 + k3 y2 y3, y2' = k1 y1 - k3 y2 y3 - k2 y2^2,
+// y3' = k2 y2^2; parameters (k1, k2, k3) per cell.
+struct RobertsonProblem {
+    static constexpr int N = 3;
+    double k1, k2, k3;
+    __device__ void load(const double *params, int64_t cell)
+    {
+        k1 = params[3 * cell + 0];
+        k2 = params[3 * cell + 1];
+        k3 = params[3 * cell + 2];
+    }
+    __device__ __forceinline__ void rhs(const double *y, double *f) const
+    {
+        const double r1 = k1 * y[0], r2 = k2 * y[1] * y[1], r3 = k3 * y[1] * y[2];
+        f[0] = -r1 + r3;
+        f[1] = r1 - r3 - r2;
+        f[2] = r2;
+    }
+    __device__ __forceinline__ void jac(const double *y, double (*J)[3]) const
+    {
+        J[0][0] = -k1;  J[0][1] = k3 * y[2];                     J[0][2] = k3 * y[1];
+        J[1][0] = k1;   J[1][1] = -k3 * y[2] - 2.0 * k2 * y[1];  J[1][2] = -k3 * y[1];
+        J[2][0] = 0.0;  J[2][1] = 2.0 * k2 * y[1];               J[2][2] = 0.0;
+    }
+};
+
+// Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
+// per-segment log-log slopes.
+struct CoolingSmem {
+    int n;
+    double gamma_heat;
+    const double *lnT, *lnLam, *slope;
+};
+
+// Heating-cooling of one gas cell (the Nyx split equation of Sec. 3.2,
+// Eq. nyxODE): T = max(e, 1 K), de/dt = F + rho (Gamma (T/1e4)^-0.7 - Lambda(T)),
+// Lambda piecewise power law through the knots (end slopes extended).
+struct CosmologyProblem {
+    static constexpr int N = 1;
+    double rho, F;
+    const CoolingSmem *tab;
+    __device__ void load(const double *params, int64_t cell)
+    {
+        rho = params[2 * cell + 0];
+        F = params[2 * cell + 1];
+    }
+    __device__ __forceinline__ void eval(double e, double &f, double &dfde) const
+    {
+        const bool floor = e < 1.0;
+        const double T = floor ? 1.0 : e;
+        const double lnT = log(T);
+        const double *x = tab->lnT;
+        const int n = tab->n;
+        int lo;
+        if (lnT <= x[0]) lo = 0;
+        else if (lnT >= x[n - 1]) lo = n - 2;
+        else {
+            lo = 0;
+            int hi = n - 1;
+            while (hi - lo > 1) {
+                const int mid = (lo + hi) >> 1;
+                if (x[mid] <= lnT) lo = mid; else hi = mid;
+            }
+        }
+        const double sl = tab->slope[lo];
+        const double lam = exp(tab->lnLam[lo] + sl * (lnT - x[lo]));
+        const double heat = tab->gamma_heat * exp(-0.7 * (lnT - LN1E4));
+        f = F + rho * (heat - lam);
+        dfde = floor ? 0.0 : rho * (-0.7 * heat - sl * lam) * rcp(T);
+    }
+    __device__ __forceinline__ void rhs(const double *y, double *f) const
+    {
+        double d;
+        eval(y[0], f[0], d);
+    }
+    __device__ __forceinline__ void jac(const double *y, double (*J)[1]) const
+    {
+        double f;
+        eval(y[0], f, J[0][0]);
+    }
+};
+
+template <class Prob>
+struct ThreadCell {
+    static constexpr int N = Prob::N;
+    Prob prob;
+    double v[NVEC][N];
+    double M[N][N];
+    double atol[N];
+    double *yg;   // this cell's state in global memory
+
+    __device__ __forceinline__ void load_y(int s)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[s][i] = yg[i];
+    }
+    __device__ __forceinline__ void store_y(int s)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) yg[i] = v[s][i];
+    }
+    __device__ __forceinline__ void rhs(int a, int b) { prob.rhs(v[a], v[b]); }
+    __device__ __forceinline__ bool all_finite(int a) const
+    {
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i) ok = ok && (fabs(v[a][i]) <= 1.7e308);
+        return ok;
+    }
+    __device__ __forceinline__ void set_weights(int a, double rtol)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[V_W][i] = rcp(rtol * fabs(v[a][i]) + atol[i]);
+    }
+    // squared WRMS norm of slot a; a may be a runtime Nordsieck column
+    __device__ __forceinline__ double wrms2(int a) const
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 0; j < NVEC; ++j) {
+            if (j == a) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) { const double t = v[j][i] * v[V_W][i]; s += t * t; }
+            }
+        }
+        return s * (1.0 / N);
+    }
+    __device__ __forceinline__ double wrms2_lin(double a, int va, double b, int vb) const
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double t = (a * v[va][i] + b * v[vb][i]) * v[V_W][i];
+            s += t * t;
+        }
+        return s * (1.0 / N);
+    }
+    __device__ __forceinline__ void axpby(int o, double a, int va, double b, int vb)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[o][i] = a * v[va][i] + b * v[vb][i];
+    }
+    __device__ __forceinline__ void scale(int o, double a, int va)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[o][i] = a * v[va][i];
+    }
+    __device__ __forceinline__ void predict(int q)
+    {
+#pragma unroll
+        for (int k = 0; k < QMAX; ++k)
+#pragma unroll
+            for (int j = QMAX; j >= 1; --j)
+                if (k < q && j > k && j <= q)
+#pragma unroll
+                    for (int i = 0; i < N; ++i) v[j - 1][i] += v[j][i];
+    }
+    __device__ __forceinline__ void unpredict(int q)
+    {
+#pragma unroll
+        for (int k = QMAX - 1; k >= 0; --k)
+#pragma unroll
+            for (int j = 1; j <= QMAX; ++j)
+                if (k < q && j > k && j <= q)
+#pragma unroll
+                    for (int i = 0; i < N; ++i) v[j - 1][i] -= v[j][i];
+    }
+    __device__ __forceinline__ void rescale(int q, double eta)
+    {
+        double f = 1.0;
+#pragma unroll
+        for (int j = 1; j <= QMAX; ++j) {
+            f *= eta;
+            if (j <= q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] *= f;
+        }
+    }
+    __device__ __forceinline__ void correct(int q, const double *l)
+    {
+#pragma unroll
+        for (int j = 0; j <= QMAX; ++j)
+            if (j <= q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] += l[j] * v[V_ACOR][i];
+    }
+    __device__ __forceinline__ void order_increase(int q, const double *l, double inv_xi)
+    {
+#pragma unroll
+        for (int j = 1; j <= QMAX; ++j) {
+            if (j == q + 1)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] = 0.0;
+            if (j <= q + 1) {
+                const double c = l[j - 1] * inv_xi;
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] += c * v[V_ACOR][i];
+            }
+        }
+    }
+    __device__ __forceinline__ void order_decrease(int q, const double *e)
+    {
+        double zq[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) zq[i] = 0.0;
+#pragma unroll
+        for (int j = 2; j <= QMAX; ++j)
+            if (j == q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) zq[i] = v[j][i];
+#pragma unroll
+        for (int j = 1; j < QMAX; ++j)
+            if (j < q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] -= e[j - 1] * zq[i];
+#pragma unroll
+        for (int j = 2; j <= QMAX; ++j)
+            if (j == q)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] = 0.0;
+    }
+    __device__ __forceinline__ void restart(double h)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[1][i] = h * v[V_F][i];
+#pragma unroll
+        for (int j = 2; j <= QMAX; ++j)
+#pragma unroll
+            for (int i = 0; i < N; ++i) v[j][i] = 0.0;
+    }
+    __device__ __forceinline__ void newton_init()
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) { v[V_ACOR][i] = 0.0; v[V_Y][i] = v[V_Z0][i]; }
+    }
+    __device__ __forceinline__ void newton_residual(double h, double il1)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+            v[V_DEL][i] = (h * v[V_F][i] - v[V_Z1][i]) * il1 - v[V_ACOR][i];
+    }
+    __device__ __forceinline__ double newton_update(double c)
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            const double d = v[V_DEL][i] * c;
+            v[V_ACOR][i] += d;
+            v[V_Y][i] = v[V_Z0][i] + v[V_ACOR][i];
+            const double t = d * v[V_W][i];
+            s += t * t;
+        }
+        return s * (1.0 / N);
+    }
+    // f(z0) into slot fo, J at z0, M = I - gamma J, in-register LU with row
+    // partial pivoting (first index of largest magnitude).  Pivots are kept
+    // as an explicit permutation applied in solve().
+    int perm[N];
+    __device__ __forceinline__ int rhs_setup(int a, int fo, double gamma)
+    {
+        prob.rhs(v[a], v[fo]);
+        double J[N][N];
+        prob.jac(v[a], J);
+#pragma unroll
+        for (int i = 0; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < N; ++j) M[i][j] = (i == j ? 1.0 : 0.0) - gamma * J[i][j];
+        bool ok = true;
+#pragma unroll
+        for (int i = 0; i < N; ++i) perm[i] = i;
+#pragma unroll
+        for (int k = 0; k < N; ++k) {
+            int p = k;
+            double amax = fabs(M[k][k]);
+#pragma unroll
+            for (int i = k + 1; i < N; ++i)
+                if (fabs(M[i][k]) > amax) { amax = fabs(M[i][k]); p = i; }
+            ok = ok && (amax > 0.0) && (amax <= 1.7e308);
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) {
+                if (i == p) {
+#pragma unroll
+                    for (int j = 0; j < N; ++j) { const double t = M[k][j]; M[k][j] = M[i][j]; M[i][j] = t; }
+                    const int tp = perm[k]; perm[k] = perm[i]; perm[i] = tp;
+                }
+            }
+            const double ip = rcp(M[k][k]);
+#pragma unroll
+            for (int i = k + 1; i < N; ++i) {
+                const double lik = M[i][k] * ip;
+                M[i][k] = lik;
+#pragma unroll
+                for (int j = k + 1; j < N; ++j) M[i][j] -= lik * M[k][j];
+            }
+            M[k][k] = ip;     // keep the reciprocal pivot for the back solve
+        }
+        return ok ? 1 : 0;
+    }
+    __device__ __forceinline__ void solve(int b)
+    {
+        double x[N];
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double t = 0.0;
+#pragma unroll
+            for (int j = 0; j < N; ++j) if (perm[i] == j) t = v[b][j];
+            x[i] = t;
+        }
+#pragma unroll
+        for (int i = 1; i < N; ++i)
+#pragma unroll
+            for (int j = 0; j < i; ++j) x[i] -= M[i][j] * x[j];
+#pragma unroll
+        for (int i = N - 1; i >= 0; --i) {
+#pragma unroll
+            for (int j = i + 1; j < N; ++j) x[i] -= M[i][j] * x[j];
+            x[i] *= M[i][i];
+        }
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[b][i] = x[i];
+    }
+};
+
+}  // namespace sunb

@@ -1,0 +1,988 @@
+// Host side of the C ABI declared in include/sunb.h, and the kernels it
+// launches.  One process, one GPU, one stream per context; all workspace is
+// allocated in sunb_create (the paper's Sec. 4.3.1 measures how much
+// per-step allocation costs), except the staging buffer of
+// sunb_integrate_host, allocated on its first use.
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "sunb.h"
+#include "sunb_common.cuh"
+#include "bdf_control.cuh"
+#include "cell_thread.cuh"
+#include "cell_group.cuh"
+
+using namespace sunb;
+
+// ============================================================ device side
+
+// Cell indices handed out by a global counter (the device work queue):
+// a finished group or thread takes the next unstarted cell, so cells whose
+// step counts differ by orders of magnitude do not leave lanes idle.
+__device__ __forceinline__ long long grab_group(unsigned long long *q, int lane, unsigned mask, int L)
+{
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(q, 1ull);
+    return (long long)__shfl_sync(mask, v, 0, L);
+}
+
+__device__ __forceinline__ long long grab_thread(unsigned long long *q)
+{
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (long long)(base + rank);
+}
+
+__device__ __forceinline__ void write_stats(int32_t *stats, int32_t *status, long long cell,
+                                            const CellStats &s)
+{
+    int4 *p = reinterpret_cast<int4 *>(stats + 8 * cell);
+    p[0] = make_int4(s.nst, s.nfe, s.nje, s.nni);
+    p[1] = make_int4(s.ncf, s.nef, s.qlast, s.status);
+    if (status) status[cell] = s.status;
+}
+
+struct CoolArgs {
+    const double *knots;   // [3 * n]: lnT, lnLam, slope (n-1 used)
+    int n;
+    double gamma_heat;
+};
+
+struct MechArgs {
+    const unsigned char *tab;
+    MechTabOffsets off;
+    CellLayout lay;
+    int cells_per_cta;
+    int schedule;
+    double invN;
+    Controls ctl;
+    long long n_mech;
+    double *y_mech;
+    const double *p_mech;
+    int32_t *stats_mech, *status_mech;
+    unsigned long long *queue;   // [0] mechanism cells, [1] cosmology cells
+    // cosmology cells of a mixed launch
+    long long n_cosmo;
+    double *y_cosmo;
+    const double *p_cosmo;
+    int32_t *stats_cosmo, *status_cosmo;
+    CoolArgs cool;
+    double atol_cosmo;
+    int cool_smem_off;
+};
+
+__device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned char *src, int bytes)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const CoolArgs &c)
+{
+    double *d = reinterpret_cast<double *>(dst);
+    for (int i = threadIdx.x; i < 3 * c.n; i += blockDim.x) d[i] = c.knots[i];
+    CoolingSmem t;
+    t.n = c.n;
+    t.gamma_heat = c.gamma_heat;
+    t.lnT = d;
+    t.lnLam = d + c.n;
+    t.slope = d + 2 * c.n;
+    return t;
+}
+
+template <int L>
+__device__ __forceinline__ unsigned group_mask()
+{
+    if (L == 32) return 0xffffffffu;
+    const int w = threadIdx.x & 31;
+    return ((1u << L) - 1u) << (w & ~(L - 1));
+}
+
+// Persistent mechanism kernel: L lanes per cell, cells_per_cta cells per
+// CTA, one CTA set per SM; the cosmology cells of a mixed launch are taken
+// one per thread after the mechanism queue runs dry (the larger cells first).
+template <int L, typename MT, bool COSMO>
+__global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_bytes(smem, a.tab, a.off.bytes);
+    CoolingSmem cool;
+    if (COSMO) cool = stage_cooling(smem + a.cool_smem_off, a.cool);
+    __syncthreads();
+
+    const int gid = threadIdx.x / L;
+    GroupCell<L, MT> c;
+    c.g.lane = threadIdx.x % L;
+    c.g.mask = group_mask<L>();
+    c.tb = mech_tab_at(smem, a.off);
+    c.N = a.off.N; c.K = a.off.K; c.M = a.off.M;
+    c.invN = a.invN;
+    c.bind(smem + a.off.bytes + gid * a.lay.bytes, a.lay);
+
+    long long next = (long long)blockIdx.x * a.cells_per_cta + gid;
+    const long long stride = (long long)gridDim.x * a.cells_per_cta;
+    for (;;) {
+        long long cell;
+        if (a.schedule == SUNB_SCHED_QUEUE) cell = grab_group(a.queue, c.g.lane, c.g.mask, L);
+        else { cell = next; next += stride; }
+        if (cell >= a.n_mech) break;
+        c.P = a.p_mech[cell];
+        c.invP = rcp(c.P);
+        c.yg = a.y_mech + cell * c.N;
+        CellStats st;
+        bdf_cell(c, a.ctl, st);
+        if (c.g.lane == 0) write_stats(a.stats_mech, a.status_mech, cell, st);
+    }
+    if (COSMO) {
+        __syncwarp();
+        for (;;) {
+            const long long cell = grab_thread(a.queue + 1);
+            if (cell >= a.n_cosmo) break;
+            ThreadCell<CosmologyProblem> tc;
+            tc.prob.tab = &cool;
+            tc.prob.load(a.p_cosmo, cell);
+            tc.atol[0] = a.atol_cosmo;
+            tc.yg = a.y_cosmo + cell;
+            CellStats st;
+            bdf_cell(tc, a.ctl, st);
+            write_stats(a.stats_cosmo, a.status_cosmo, cell, st);
+        }
+    }
+}
+
+struct ThreadArgs {
+    long long n;
+    double *y;
+    const double *params;
+    int32_t *stats, *status;
+    unsigned long long *queue;
+    Controls ctl;
+    double atol[3];
+    CoolArgs cool;
+};
+
+// Thread-per-cell kernel for Robertson and cosmology batches.
+template <class Prob>
+__global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
+{
+    __shared__ __align__(16) double cool_s[3 * 256];
+    CoolingSmem cool;
+    if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
+    __syncthreads();
+    for (;;) {
+        const long long cell = grab_thread(a.queue);
+        if (cell >= a.n) break;
+        ThreadCell<Prob> tc;
+        if constexpr (Prob::N == 1) tc.prob.tab = &cool;
+        tc.prob.load(a.params, cell);
+#pragma unroll
+        for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
+        tc.yg = a.y + cell * Prob::N;
+        CellStats st;
+        bdf_cell(tc, a.ctl, st);
+        write_stats(a.stats, a.status, cell, st);
+    }
+}
+
+// Batched right-hand side (mode 0) or Jacobian (mode 1) of a mechanism:
+// one warp per cell, results to out ([n, N] or [n, N, N]).
+__global__ void __launch_bounds__(128) mech_eval_kernel(const MechArgs a, const double *y,
+                                                        double *out, long long n, int mode)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_bytes(smem, a.tab, a.off.bytes);
+    __syncthreads();
+    const int gid = threadIdx.x / 32;
+    GroupCell<32, double> c;
+    c.g.lane = threadIdx.x % 32;
+    c.g.mask = 0xffffffffu;
+    c.tb = mech_tab_at(smem, a.off);
+    c.N = a.off.N; c.K = a.off.K; c.M = a.off.M;
+    c.invN = a.invN;
+    c.bind(smem + a.off.bytes + gid * a.lay.bytes, a.lay);
+    const int N = c.N;
+    for (long long cell = (long long)blockIdx.x * a.cells_per_cta + gid; cell < n;
+         cell += (long long)gridDim.x * a.cells_per_cta) {
+        c.P = a.p_mech[cell];
+        c.invP = rcp(c.P);
+        c.yg = const_cast<double *>(y) + cell * N;
+        c.load_y(V_Y);
+        if (mode == 0) {
+            c.rhs(V_Y, V_F);
+            for (int i = c.g.lane; i < N; i += 32) out[cell * N + i] = c.V(V_F)[i];
+        } else {
+            c.template eval<true>(V_Y, V_F, -1.0, false);
+            for (int i = c.g.lane; i < N * N; i += 32) out[cell * N * N + i] = (double)c.mat[i];
+        }
+        c.g.sync();
+    }
+}
+
+template <class Prob>
+__global__ void thread_eval_kernel(const ThreadArgs a, const double *y, double *out, long long n, int mode)
+{
+    __shared__ __align__(16) double cool_s[3 * 256];
+    CoolingSmem cool;
+    if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
+    __syncthreads();
+    constexpr int N = Prob::N;
+    for (long long cell = blockIdx.x * (long long)blockDim.x + threadIdx.x; cell < n;
+         cell += (long long)gridDim.x * blockDim.x) {
+        Prob p;
+        if constexpr (N == 1) p.tab = &cool;
+        p.load(a.params, cell);
+        double yy[N], f[N], J[N][N];
+        for (int i = 0; i < N; ++i) yy[i] = y[cell * N + i];
+        if (mode == 0) {
+            p.rhs(yy, f);
+            for (int i = 0; i < N; ++i) out[cell * N + i] = f[i];
+        } else {
+            p.jac(yy, J);
+            for (int i = 0; i < N; ++i)
+                for (int j = 0; j < N; ++j) out[(cell * N + i) * N + j] = J[i][j];
+        }
+    }
+}
+
+// Batched LU factor + solve: one warp per system, matrix staged in shared memory.
+template <typename MT>
+__global__ void __launch_bounds__(128) lu_batched_kernel(int n, long long batch, MT *A, int32_t *piv,
+                                                         MT *b, int32_t *info, int per_warp_bytes)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    const int w = threadIdx.x / 32;
+    unsigned char *base = smem + w * per_warp_bytes;
+    MT *mat = reinterpret_cast<MT *>(base);
+    MT *dinv = mat + n * n;
+    MT *xs = dinv + n;
+    int32_t *perm = reinterpret_cast<int32_t *>(xs + n);
+    int32_t *pv = perm + n;
+    Grp<32> g;
+    g.lane = threadIdx.x % 32;
+    g.mask = 0xffffffffu;
+    for (long long s = (long long)blockIdx.x * (blockDim.x / 32) + w; s < batch;
+         s += (long long)gridDim.x * (blockDim.x / 32)) {
+        MT *As = A + s * n * n;
+        for (int i = g.lane; i < n * n; i += 32) mat[i] = As[i];
+        g.sync();
+        const int ok = lu_factor<32, MT>(g, mat, n, perm, dinv, pv);
+        int bad = n;
+        if (!ok) {   // first column without a usable pivot
+            for (int k = 0; k < n; ++k) {
+                if (!(fabs((double)mat[k * n + k]) > 0.0)) { bad = k; break; }
+            }
+        }
+        lu_solve<32, MT, MT>(g, mat, n, perm, dinv, xs, b + s * n);
+        for (int i = g.lane; i < n * n; i += 32) As[i] = mat[i];
+        for (int i = g.lane; i < n; i += 32) piv[s * n + i] = pv[i];
+        if (g.lane == 0) info[s] = ok ? 0 : bad + 1;
+        g.sync();
+    }
+}
+
+struct DevTotals {
+    unsigned long long sum[6];
+    int max_nst;
+    int worst;
+    unsigned long long nfail;
+};
+
+__global__ void totals_kernel(const int32_t *stats, long long n, DevTotals *t)
+{
+    unsigned long long s[6] = {0, 0, 0, 0, 0, 0}, nf = 0;
+    int mx = 0, worst = 0;
+    for (long long c = blockIdx.x * (long long)blockDim.x + threadIdx.x; c < n;
+         c += (long long)gridDim.x * blockDim.x) {
+        const int4 a = reinterpret_cast<const int4 *>(stats)[2 * c];
+        const int4 b = reinterpret_cast<const int4 *>(stats)[2 * c + 1];
+        s[0] += a.x; s[1] += a.y; s[2] += a.z; s[3] += a.w; s[4] += b.x; s[5] += b.y;
+        mx = max(mx, a.x);
+        worst = min(worst, b.w);
+        nf += (b.w != 0);
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+#pragma unroll
+        for (int i = 0; i < 6; ++i) s[i] += __shfl_xor_sync(0xffffffffu, s[i], o);
+        nf += __shfl_xor_sync(0xffffffffu, nf, o);
+        mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+        worst = min(worst, __shfl_xor_sync(0xffffffffu, worst, o));
+    }
+    if ((threadIdx.x & 31) == 0) {
+        for (int i = 0; i < 6; ++i) atomicAdd(&t->sum[i], s[i]);
+        atomicAdd(&t->nfail, nf);
+        atomicMax(&t->max_nst, mx);
+        atomicMin(&t->worst, worst);
+    }
+}
+
+// ============================================================ host side
+
+struct sunb_ctx {
+    int kind = 0;
+    long long C = 0, Cc = 0;         // mechanism (or Robertson/cosmology) cells, cosmology cells (mixed)
+    int N = 0;
+    int max_order = 5, max_steps = 100000, precision = SUNB_FP64, L = 32, schedule = SUNB_SCHED_QUEUE;
+    bool autotune = false, tuned = false;
+    cudaStream_t stream = nullptr;
+    int device = 0, num_sms = 148;
+    double rtol = 1e-6;
+    std::vector<double> atol;        // N (+1 for mixed)
+    const double *params = nullptr;
+    // mechanism
+    MechTabOffsets off{};
+    std::vector<unsigned char> blob;
+    unsigned char *d_tab = nullptr;
+    CellLayout lay{};
+    int cells_per_cta = 1, ctas_per_sm = 1;
+    // cosmology
+    double *d_cool = nullptr;
+    int nknots = 0;
+    double gamma_heat = 0.0;
+    // workspace
+    int32_t *d_stats = nullptr;
+    unsigned long long *d_queue = nullptr;
+    DevTotals *d_totals = nullptr;
+    double *d_ybuf = nullptr;
+    int32_t *d_sbuf = nullptr;
+    double *d_tune = nullptr;        // autotuning sample (copy of the first cells)
+    long long tune_cells = 0;
+    float tune_ms[3][2] = {{0}};     // trial times, L = 8/16/32 x two CTA sizes
+    long long launches = 0;
+    std::string err;
+};
+
+static std::string g_create_error = "no error";
+
+static int fail(sunb_ctx *ctx, int code, const std::string &msg)
+{
+    if (ctx) ctx->err = msg; else g_create_error = msg;
+    return code;
+}
+
+#define CU(call)                                                                        \
+    do {                                                                                \
+        cudaError_t e_ = (call);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(ctx, SUNB_CUDA_ERROR, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+static int align16(int x) { return (x + 15) & ~15; }
+
+static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
+{
+    const int K = m->n_species, M = m->n_reactions, N = K + 1;
+    if (K < 1 || K > 63 || M < 1 || M > 4096)
+        return fail(ctx, SUNB_ILL_INPUT, "mechanism: need 1 <= n_species <= 63 and 1 <= n_reactions <= 4096");
+    if (!m->W || !m->nasa || !m->react || !m->prod || !m->lnA || !m->beta || !m->Ea)
+        return fail(ctx, SUNB_ILL_INPUT, "mechanism: a table pointer is NULL");
+    std::vector<std::vector<std::pair<int, int>>> inc(K);
+    std::vector<uint32_t> ridx(2 * M);
+    for (int j = 0; j < M; ++j) {
+        int r[3], p[3], nr = 0, np = 0;
+        for (int s = 0; s < 3; ++s) {
+            r[s] = m->react[3 * j + s];
+            p[s] = m->prod[3 * j + s];
+            if (r[s] < -1 || r[s] >= K || p[s] < -1 || p[s] >= K)
+                return fail(ctx, SUNB_ILL_INPUT, "mechanism: species index out of range in reaction " + std::to_string(j));
+            nr += r[s] >= 0;
+            np += p[s] >= 0;
+        }
+        if (nr == 0 || np == 0)
+            return fail(ctx, SUNB_ILL_INPUT, "mechanism: reaction " + std::to_string(j) + " lacks reactants or products");
+        int rs[3], ps[3];
+        for (int s = 0; s < 3; ++s) { rs[s] = r[s] >= 0 ? r[s] : K; ps[s] = p[s] >= 0 ? p[s] : K; }
+        // keep used slots first so that position 0 is always a species
+        std::stable_partition(rs, rs + 3, [K](int v) { return v != K; });
+        std::stable_partition(ps, ps + 3, [K](int v) { return v != K; });
+        const int dnu = np - nr;
+        ridx[2 * j] = (uint32_t)rs[0] | ((uint32_t)rs[1] << 8) | ((uint32_t)rs[2] << 16) | ((uint32_t)ps[0] << 24);
+        ridx[2 * j + 1] = (uint32_t)ps[1] | ((uint32_t)ps[2] << 8) | ((uint32_t)(dnu + 8) << 16);
+        int net[64] = {0};
+        for (int s = 0; s < 3; ++s) {
+            if (r[s] >= 0) net[r[s]] -= 1;
+            if (p[s] >= 0) net[p[s]] += 1;
+        }
+        for (int k = 0; k < K; ++k)
+            if (net[k] != 0) inc[k].push_back({j, net[k]});
+    }
+    int nnz = 0;
+    for (int k = 0; k < K; ++k) nnz += (int)inc[k].size();
+
+    MechTabOffsets o{};
+    o.K = K; o.M = M; o.N = N; o.nnz = nnz;
+    int off = 0;
+    auto take = [&](int bytes) { const int r = off; off = align16(off + bytes); return r; };
+    o.invW = take(8 * K); o.W = take(8 * K); o.cpc = take(8 * 5 * K); o.hc = take(8 * 6 * K);
+    o.sc = take(8 * 6 * K); o.dcp = take(8 * 4 * K); o.rpar = take(8 * 3 * M); o.atol = take(8 * N);
+    o.inc_nu = take(8 * std::max(nnz, 1)); o.ridx = take(4 * 2 * M); o.inc_ptr = take(4 * (K + 1));
+    o.inc_j = take(4 * std::max(nnz, 1));
+    o.bytes = off;
+    std::vector<unsigned char> blob(off, 0);
+    auto D = [&](int o_) { return reinterpret_cast<double *>(blob.data() + o_); };
+    auto I = [&](int o_) { return reinterpret_cast<int32_t *>(blob.data() + o_); };
+    for (int k = 0; k < K; ++k) {
+        const double *a = m->nasa + 7 * k;
+        if (!(m->W[k] > 0.0)) return fail(ctx, SUNB_ILL_INPUT, "mechanism: molecular weights must be positive");
+        D(o.invW)[k] = 1.0 / m->W[k];
+        D(o.W)[k] = m->W[k];
+        for (int i = 0; i < 5; ++i) D(o.cpc)[5 * k + i] = a[i];
+        const double hc[6] = {a[0], a[1] / 2.0, a[2] / 3.0, a[3] / 4.0, a[4] / 5.0, a[5]};
+        const double sc[6] = {a[0], a[1], a[2] / 2.0, a[3] / 3.0, a[4] / 4.0, a[6]};
+        const double dc[4] = {a[1], 2.0 * a[2], 3.0 * a[3], 4.0 * a[4]};
+        for (int i = 0; i < 6; ++i) { D(o.hc)[6 * k + i] = hc[i]; D(o.sc)[6 * k + i] = sc[i]; }
+        for (int i = 0; i < 4; ++i) D(o.dcp)[4 * k + i] = dc[i];
+    }
+    for (int j = 0; j < M; ++j) {
+        D(o.rpar)[3 * j] = m->lnA[j];
+        D(o.rpar)[3 * j + 1] = m->beta[j];
+        D(o.rpar)[3 * j + 2] = m->Ea[j] / RC;
+    }
+    for (int i = 0; i < N; ++i) D(o.atol)[i] = 1e-10;
+    int e = 0;
+    for (int k = 0; k < K; ++k) {
+        I(o.inc_ptr)[k] = e;
+        for (auto &pr : inc[k]) { I(o.inc_j)[e] = pr.first; D(o.inc_nu)[e] = (double)pr.second; ++e; }
+    }
+    I(o.inc_ptr)[K] = e;
+    std::memcpy(blob.data() + o.ridx, ridx.data(), 4 * 2 * M);
+    ctx->off = o;
+    ctx->blob.swap(blob);
+    return SUNB_SUCCESS;
+}
+
+static CellLayout make_layout(int N, int K, int M, int mt)
+{
+    CellLayout l{};
+    l.NP = (N + 1) & ~1;
+    int off = 0;
+    auto take = [&](int bytes) { const int r = off; off = align16(off + bytes); return r; };
+    l.vec = take(8 * NVEC * l.NP);
+    l.mat = take(mt * N * N);
+    l.perm = take(4 * N);
+    l.xs = take(mt * 2 * N);
+    l.sp = take(8 * (4 * (K + 1) + 4 * K));
+    l.rq = take(8 * M);
+    l.dq = take(8 * 7 * M);
+    l.bytes = off;
+    return l;
+}
+
+template <int L, typename MT, bool COSMO>
+static void *mech_kernel_ptr() { return (void *)mech_kernel<L, MT, COSMO>; }
+
+static void *pick_mech_kernel(int L, int precision, bool cosmo)
+{
+    const bool f = precision == SUNB_MIXED32;
+#define PICK(LL)                                                                                   \
+    if (L == LL) return f ? (cosmo ? mech_kernel_ptr<LL, float, true>() : mech_kernel_ptr<LL, float, false>()) \
+                          : (cosmo ? mech_kernel_ptr<LL, double, true>() : mech_kernel_ptr<LL, double, false>());
+    PICK(8) PICK(16) PICK(32)
+#undef PICK
+    return nullptr;
+}
+
+static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(8 * 3 * c->nknots) : 0; }
+
+// Cells per CTA for lanes-per-cell L: the count that keeps the most cells
+// resident per SM within the shared-memory budget (whole warps, <= 1024 threads).
+static int configure_mech(sunb_ctx *ctx, int L, int force_cpc = 0)
+{
+    const int mt = ctx->precision == SUNB_MIXED32 ? 4 : 8;
+    ctx->lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, mt);
+    const bool cosmo = ctx->kind == SUNB_MIXED;
+    int dev_optin = 0, sm_bytes = 0;
+    CU(cudaDeviceGetAttribute(&dev_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    CU(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
+    const int fixed = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0);
+    int best_c = 0, best_res = -1;
+    for (int c = std::max(1, 32 / L); c * L <= 256; c += std::max(1, 32 / L)) {
+        const int bytes = fixed + c * ctx->lay.bytes;
+        if (bytes > dev_optin) break;
+        int blocks = sm_bytes / (bytes + 1024);
+        blocks = std::min(blocks, 2048 / (c * L));
+        const int res = blocks * c;
+        if (res > best_res) { best_res = res; best_c = c; }
+    }
+    if (best_c == 0)
+        return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for shared memory at this precision and mapping");
+    if (force_cpc > 0) {
+        if (force_cpc * L > 256 || (force_cpc * L) % 32 != 0 || fixed + force_cpc * ctx->lay.bytes > dev_optin)
+            return fail(ctx, SUNB_ILL_INPUT, "cells per CTA does not fit");
+        best_c = force_cpc;
+    }
+    ctx->L = L;
+    ctx->cells_per_cta = best_c;
+    const int bytes = fixed + best_c * ctx->lay.bytes;
+    void *k = pick_mech_kernel(L, ctx->precision, cosmo);
+    CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, best_c * L, bytes));
+    ctx->ctas_per_sm = std::max(1, occ);
+    return SUNB_SUCCESS;
+}
+
+static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
+{
+    MechArgs a{};
+    a.tab = ctx->d_tab;
+    a.off = ctx->off;
+    a.lay = ctx->lay;
+    a.cells_per_cta = ctx->cells_per_cta;
+    a.schedule = ctx->schedule;
+    a.invN = 1.0 / ctx->off.N;
+    a.ctl.rtol = ctx->rtol;
+    a.ctl.t0 = t0;
+    a.ctl.tout = tout;
+    a.ctl.max_steps = ctx->max_steps;
+    a.ctl.max_order = ctx->max_order;
+    a.queue = ctx->d_queue;
+    const bool mixed = ctx->kind == SUNB_MIXED;
+    a.n_mech = ctx->C;
+    a.y_mech = y ? y + (mixed ? ctx->Cc : 0) : nullptr;
+    a.p_mech = ctx->params ? ctx->params + (mixed ? 2 * ctx->Cc : 0) : nullptr;
+    a.stats_mech = ctx->d_stats + (mixed ? 8 * ctx->Cc : 0);
+    a.status_mech = status ? status + (mixed ? ctx->Cc : 0) : nullptr;
+    if (mixed) {
+        a.n_cosmo = ctx->Cc;
+        a.y_cosmo = y;
+        a.p_cosmo = ctx->params;
+        a.stats_cosmo = ctx->d_stats;
+        a.status_cosmo = status;
+        a.cool.knots = ctx->d_cool;
+        a.cool.n = ctx->nknots;
+        a.cool.gamma_heat = ctx->gamma_heat;
+        a.atol_cosmo = ctx->atol[ctx->off.N];
+        a.cool_smem_off = ctx->off.bytes;
+    }
+    return a;
+}
+
+static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status,
+                       long long n_mech_override = -1)
+{
+    const bool cosmo = ctx->kind == SUNB_MIXED;
+    MechArgs a = mech_args(ctx, y, t0, tout, status);
+    if (n_mech_override >= 0) {   // autotuning trial: mechanism cells only, from a scratch copy
+        a.n_mech = n_mech_override;
+        a.y_mech = y;
+        a.p_mech = ctx->params + (cosmo ? 2 * ctx->Cc : 0);
+        a.n_cosmo = 0;
+    }
+    if (cosmo) {   // mechanism tables, cooling table, then the cells
+        a.cool_smem_off = ctx->off.bytes;
+        a.off.bytes = ctx->off.bytes;
+    }
+    const int fixed = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0);
+    const int bytes = fixed + ctx->cells_per_cta * ctx->lay.bytes;
+    const int threads = ctx->cells_per_cta * ctx->L;
+    const int grid = ctx->num_sms * ctx->ctas_per_sm;
+    CU(cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    void *k = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
+    // the cells start after the cooling table in a mixed launch
+    CellLayout lay = ctx->lay;
+    if (cosmo) {
+        const int shift = cool_bytes(ctx);
+        // GroupCell::bind takes offsets from (tables + gid * cell bytes); shift every field
+        lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
+        lay.sp += shift; lay.rq += shift; lay.dq += shift;
+        a.lay = lay;
+        a.lay.bytes = ctx->lay.bytes;
+    }
+    void *args[] = {&a};
+    CU(cudaLaunchKernel(k, dim3(grid), dim3(threads), args, bytes, ctx->stream));
+    ctx->launches++;
+    return SUNB_SUCCESS;
+}
+
+static ThreadArgs thread_args(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
+{
+    ThreadArgs a{};
+    a.n = ctx->C;
+    a.y = y;
+    a.params = ctx->params;
+    a.stats = ctx->d_stats;
+    a.status = status;
+    a.queue = ctx->d_queue;
+    a.ctl.rtol = ctx->rtol;
+    a.ctl.t0 = t0;
+    a.ctl.tout = tout;
+    a.ctl.max_steps = ctx->max_steps;
+    a.ctl.max_order = ctx->max_order;
+    for (int i = 0; i < ctx->N && i < 3; ++i) a.atol[i] = ctx->atol[i];
+    a.cool.knots = ctx->d_cool;
+    a.cool.n = ctx->nknots;
+    a.cool.gamma_heat = ctx->gamma_heat;
+    return a;
+}
+
+static int launch_thread(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
+{
+    ThreadArgs a = thread_args(ctx, y, t0, tout, status);
+    CU(cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    const int threads = 256;
+    void *k = ctx->kind == SUNB_ROBERTSON ? (void *)thread_kernel<RobertsonProblem>
+                                          : (void *)thread_kernel<CosmologyProblem>;
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0));
+    long long want = (ctx->C + threads - 1) / threads;
+    const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ)));
+    void *args[] = {&a};
+    CU(cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, ctx->stream));
+    ctx->launches++;
+    return SUNB_SUCCESS;
+}
+
+template <typename MT>
+static int lu_batched(int32_t n, int64_t batch, MT *A, int32_t *piv, MT *b, int32_t *info, void *stream)
+{
+    sunb_ctx *ctx = nullptr;
+    if (n < 1 || n > 64 || batch < 0 || !A || !piv || !b || !info)
+        return fail(nullptr, SUNB_ILL_INPUT, "lu: need 1 <= n <= 64 and non-NULL arrays");
+    if (batch == 0) return SUNB_SUCCESS;
+    const int per_warp = align16((int)sizeof(MT) * (n * n + 2 * n) + 8 * n);
+    const int warps = 4;
+    const int bytes = warps * per_warp;
+    CU(cudaFuncSetAttribute((void *)lu_batched_kernel<MT>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int dev = 0, sms = 148;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int grid = (int)std::min<long long>((batch + warps - 1) / warps, 16LL * sms);
+    lu_batched_kernel<MT><<<grid, 32 * warps, bytes, (cudaStream_t)stream>>>(n, batch, A, piv, b, info, per_warp);
+    CU(cudaGetLastError());
+    return SUNB_SUCCESS;
+}
+
+
+// Autotuner for the mechanism mapping (lanes per cell L and cells per CTA):
+// on the first integration of a context created with lanes_per_cell = 0,
+// the first tune_cells cells are copied to scratch and integrated once per
+// candidate (L = 8, 16, 32; the resident-maximising CTA size and half of it),
+// timed with CUDA events on the context's stream; the fastest is kept.
+// The trials are synchronous and leave the caller's state untouched.
+static int autotune(sunb_ctx *ctx, const double *dev_y, double t0, double tout)
+{
+    const bool mixed = ctx->kind == SUNB_MIXED;
+    const double *ysrc = dev_y + (mixed ? ctx->Cc : 0);
+    const size_t bytes = 8 * (size_t)ctx->tune_cells * ctx->N;
+    cudaEvent_t e0, e1;
+    CU(cudaEventCreate(&e0));
+    CU(cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestL = ctx->L, bestc = ctx->cells_per_cta;
+    const int Ls[3] = {8, 16, 32};
+    for (int li = 0; li < 3; ++li) {
+        int rc = configure_mech(ctx, Ls[li]);
+        if (rc != SUNB_SUCCESS) continue;
+        const int cmax = ctx->cells_per_cta;
+        const int step = std::max(1, 32 / Ls[li]);
+        int cands[2] = {cmax, std::max(step, (cmax / 2) / step * step)};
+        for (int ci = 0; ci < 2; ++ci) {
+            if (ci == 1 && cands[1] == cands[0]) { ctx->tune_ms[li][ci] = -1.0f; continue; }
+            if (configure_mech(ctx, Ls[li], cands[ci]) != SUNB_SUCCESS) continue;
+            CU(cudaMemcpyAsync(ctx->d_tune, ysrc, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
+            CU(cudaEventRecord(e0, ctx->stream));
+            int r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, ctx->tune_cells);
+            CU(cudaEventRecord(e1, ctx->stream));
+            CU(cudaEventSynchronize(e1));
+            if (r != SUNB_SUCCESS) return r;
+            float ms = 0.0f;
+            CU(cudaEventElapsedTime(&ms, e0, e1));
+            ctx->tune_ms[li][ci] = ms;
+            if (ms < best) { best = ms; bestL = Ls[li]; bestc = cands[ci]; }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ctx->tuned = true;
+    return configure_mech(ctx, bestL, bestc);
+}
+
+extern "C" {
+
+const char *sunb_version(void) { return "sunb 0.1 (sm_103a)"; }
+
+const char *sunb_last_error(const sunb_ctx *ctx) { return ctx ? ctx->err.c_str() : g_create_error.c_str(); }
+
+int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
+{
+    if (!out) return fail(nullptr, SUNB_ILL_INPUT, "out is NULL");
+    *out = nullptr;
+    if (!prob) return fail(nullptr, SUNB_ILL_INPUT, "problem is NULL");
+    sunb_ctx *ctx = new (std::nothrow) sunb_ctx;
+    if (!ctx) return fail(nullptr, SUNB_MEM_FAIL, "host allocation failed");
+    auto bail = [&](int code) { g_create_error = ctx->err; sunb_destroy(ctx); return code; };
+    ctx->kind = prob->kind;
+    ctx->C = prob->n_cells;
+    ctx->Cc = prob->kind == SUNB_MIXED ? prob->n_cells_cosmo : 0;
+    ctx->max_order = prob->max_order ? prob->max_order : 5;
+    ctx->max_steps = prob->max_steps ? prob->max_steps : 100000;
+    ctx->precision = prob->precision;
+    ctx->schedule = prob->schedule;
+    ctx->stream = (cudaStream_t)stream;
+    if (prob->kind < SUNB_ROBERTSON || prob->kind > SUNB_MIXED) { fail(ctx, SUNB_ILL_INPUT, "unknown kind"); return bail(SUNB_ILL_INPUT); }
+    if (ctx->C < 0 || ctx->Cc < 0 || (ctx->C == 0 && ctx->Cc == 0)) { fail(ctx, SUNB_ILL_INPUT, "need at least one cell"); return bail(SUNB_ILL_INPUT); }
+    if (ctx->max_order < 1 || ctx->max_order > 5) { fail(ctx, SUNB_ILL_INPUT, "max_order must be 1..5"); return bail(SUNB_ILL_INPUT); }
+    if (ctx->max_steps < 1) { fail(ctx, SUNB_ILL_INPUT, "max_steps must be positive"); return bail(SUNB_ILL_INPUT); }
+    if (prob->precision != SUNB_FP64 && prob->precision != SUNB_MIXED32) { fail(ctx, SUNB_ILL_INPUT, "unknown precision"); return bail(SUNB_ILL_INPUT); }
+    if (prob->schedule != SUNB_SCHED_QUEUE && prob->schedule != SUNB_SCHED_STATIC) { fail(ctx, SUNB_ILL_INPUT, "unknown schedule"); return bail(SUNB_ILL_INPUT); }
+    if (prob->record_adjoint) { fail(ctx, SUNB_ILL_INPUT, "record_adjoint is not supported by this build"); return bail(SUNB_ILL_INPUT); }
+    const int lpc = prob->lanes_per_cell;
+    if (lpc != 0 && lpc != 8 && lpc != 16 && lpc != 32) { fail(ctx, SUNB_ILL_INPUT, "lanes_per_cell must be 0, 8, 16 or 32"); return bail(SUNB_ILL_INPUT); }
+    int rc;
+    if (cudaGetDevice(&ctx->device) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "no CUDA device"); return bail(SUNB_CUDA_ERROR); }
+    cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
+
+    if (ctx->kind == SUNB_ROBERTSON) ctx->N = 3;
+    if (ctx->kind == SUNB_COSMOLOGY) ctx->N = 1;
+    if (ctx->kind == SUNB_MECHANISM || ctx->kind == SUNB_MIXED) {
+        if (!prob->mech) { fail(ctx, SUNB_ILL_INPUT, "mechanism is NULL"); return bail(SUNB_ILL_INPUT); }
+        if ((rc = build_mech_blob(ctx, prob->mech)) != SUNB_SUCCESS) return bail(rc);
+        ctx->N = ctx->off.N;
+    }
+    if (ctx->kind == SUNB_COSMOLOGY || ctx->kind == SUNB_MIXED) {
+        const sunb_cooling_table *t = prob->table;
+        if (!t || !t->lnT || !t->lnLam || t->n_knots < 2 || t->n_knots > 256) {
+            fail(ctx, SUNB_ILL_INPUT, "cooling table missing or with n_knots outside 2..256");
+            return bail(SUNB_ILL_INPUT);
+        }
+        std::vector<double> k(3 * t->n_knots, 0.0);
+        for (int i = 0; i < t->n_knots; ++i) {
+            k[i] = t->lnT[i];
+            k[t->n_knots + i] = t->lnLam[i];
+            if (i > 0 && !(t->lnT[i] > t->lnT[i - 1])) { fail(ctx, SUNB_ILL_INPUT, "cooling knots must increase"); return bail(SUNB_ILL_INPUT); }
+        }
+        for (int i = 0; i + 1 < t->n_knots; ++i)
+            k[2 * t->n_knots + i] = (t->lnLam[i + 1] - t->lnLam[i]) / (t->lnT[i + 1] - t->lnT[i]);
+        ctx->nknots = t->n_knots;
+        ctx->gamma_heat = t->gamma_heat;
+        if (cudaMalloc(&ctx->d_cool, 8 * k.size()) != cudaSuccess) { fail(ctx, SUNB_MEM_FAIL, "cudaMalloc cooling table"); return bail(SUNB_MEM_FAIL); }
+        if (cudaMemcpy(ctx->d_cool, k.data(), 8 * k.size(), cudaMemcpyHostToDevice) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "copy cooling table"); return bail(SUNB_CUDA_ERROR); }
+    }
+    ctx->atol.assign(ctx->N + (ctx->kind == SUNB_MIXED ? 1 : 0), 1e-10);
+    const long long ncell = ctx->C + ctx->Cc;
+    if (cudaMalloc(&ctx->d_stats, 32 * (size_t)ncell) != cudaSuccess ||
+        cudaMalloc(&ctx->d_queue, 64) != cudaSuccess ||
+        cudaMalloc(&ctx->d_totals, sizeof(DevTotals)) != cudaSuccess) {
+        fail(ctx, SUNB_MEM_FAIL, "cudaMalloc workspace");
+        return bail(SUNB_MEM_FAIL);
+    }
+    cudaMemset(ctx->d_stats, 0, 32 * (size_t)ncell);
+    if (ctx->kind == SUNB_MECHANISM || ctx->kind == SUNB_MIXED) {
+        if (cudaMalloc(&ctx->d_tab, ctx->off.bytes) != cudaSuccess) { fail(ctx, SUNB_MEM_FAIL, "cudaMalloc tables"); return bail(SUNB_MEM_FAIL); }
+        if (cudaMemcpy(ctx->d_tab, ctx->blob.data(), ctx->off.bytes, cudaMemcpyHostToDevice) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "copy tables"); return bail(SUNB_CUDA_ERROR); }
+        int L = lpc ? lpc : (ctx->off.N > 32 ? 32 : 16);
+        ctx->autotune = lpc == 0;
+        if ((rc = configure_mech(ctx, L)) != SUNB_SUCCESS) return bail(rc);
+        if (ctx->autotune) {
+            // enough cells to fill the GPU twice at the densest mapping
+            ctx->tune_cells = std::min<long long>(ctx->C, 2LL * ctx->num_sms * 32);
+            if (ctx->tune_cells >= 1 &&
+                cudaMalloc(&ctx->d_tune, 8 * (size_t)ctx->tune_cells * ctx->N) != cudaSuccess) {
+                fail(ctx, SUNB_MEM_FAIL, "cudaMalloc autotuning scratch");
+                return bail(SUNB_MEM_FAIL);
+            }
+        }
+    }
+    *out = ctx;
+    return SUNB_SUCCESS;
+}
+
+int sunb_destroy(sunb_ctx *ctx)
+{
+    if (!ctx) return SUNB_SUCCESS;
+    cudaFree(ctx->d_tab);
+    cudaFree(ctx->d_cool);
+    cudaFree(ctx->d_stats);
+    cudaFree(ctx->d_queue);
+    cudaFree(ctx->d_totals);
+    cudaFree(ctx->d_ybuf);
+    cudaFree(ctx->d_sbuf);
+    cudaFree(ctx->d_tune);
+    delete ctx;
+    return SUNB_SUCCESS;
+}
+
+int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const double *host_atol)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!(rtol > 0.0) || !(rtol < 1.0)) return fail(ctx, SUNB_ILL_INPUT, "rtol must lie in (0, 1)");
+    for (size_t i = 0; i < ctx->atol.size(); ++i) {
+        const double a = host_atol ? host_atol[i] : atol_scalar;
+        if (!(a > 0.0) || !std::isfinite(a)) return fail(ctx, SUNB_ILL_INPUT, "atol must be positive and finite");
+        ctx->atol[i] = a;
+    }
+    ctx->rtol = rtol;
+    if (ctx->d_tab) {
+        double *at = reinterpret_cast<double *>(ctx->blob.data() + ctx->off.atol);
+        for (int i = 0; i < ctx->off.N; ++i) at[i] = ctx->atol[i];
+        CU(cudaMemcpyAsync(ctx->d_tab + ctx->off.atol, at, 8 * ctx->off.N, cudaMemcpyHostToDevice, ctx->stream));
+        CU(cudaStreamSynchronize(ctx->stream));
+    }
+    return SUNB_SUCCESS;
+}
+
+int sunb_set_params(sunb_ctx *ctx, const double *dev_params)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_params) return fail(ctx, SUNB_ILL_INPUT, "params is NULL");
+    ctx->params = dev_params;
+    return SUNB_SUCCESS;
+}
+
+int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t *dev_status)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_y) return fail(ctx, SUNB_ILL_INPUT, "y is NULL");
+    if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
+    if (!std::isfinite(t0) || !std::isfinite(tout) || tout < t0)
+        return fail(ctx, SUNB_ILL_INPUT, "need finite t0 <= tout");
+    if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)
+        return launch_thread(ctx, dev_y, t0, tout, dev_status);
+    if (ctx->autotune && !ctx->tuned && ctx->tune_cells > 0 && tout > t0) {
+        const int rc = autotune(ctx, dev_y, t0, tout);
+        if (rc != SUNB_SUCCESS) return rc;
+    }
+    return launch_mech(ctx, dev_y, t0, tout, dev_status);
+}
+
+int sunb_get_totals(sunb_ctx *ctx, sunb_totals *host_totals, int32_t *dev_cell_stats)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    const long long n = ctx->C + ctx->Cc;
+    DevTotals init{};
+    init.max_nst = 0;
+    init.worst = 0;
+    CU(cudaMemcpyAsync(ctx->d_totals, &init, sizeof(init), cudaMemcpyHostToDevice, ctx->stream));
+    const int grid = (int)std::min<long long>((n + 255) / 256, 4LL * ctx->num_sms);
+    totals_kernel<<<std::max(1, grid), 256, 0, ctx->stream>>>(ctx->d_stats, n, ctx->d_totals);
+    CU(cudaGetLastError());
+    ctx->launches++;
+    DevTotals t{};
+    CU(cudaMemcpyAsync(&t, ctx->d_totals, sizeof(t), cudaMemcpyDeviceToHost, ctx->stream));
+    if (dev_cell_stats)
+        CU(cudaMemcpyAsync(dev_cell_stats, ctx->d_stats, 32 * (size_t)n, cudaMemcpyDeviceToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (host_totals) {
+        host_totals->nst = (int64_t)t.sum[0];
+        host_totals->nfe = (int64_t)t.sum[1];
+        host_totals->nje = (int64_t)t.sum[2];
+        host_totals->nni = (int64_t)t.sum[3];
+        host_totals->ncf = (int64_t)t.sum[4];
+        host_totals->nef = (int64_t)t.sum[5];
+        host_totals->max_nst = t.max_nst;
+        host_totals->worst_status = t.worst;
+        host_totals->n_failed = (int64_t)t.nfail;
+    }
+    return t.worst;
+}
+
+int sunb_integrate_host(sunb_ctx *ctx, double *host_y, double t0, double tout, int32_t *host_status)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!host_y) return fail(ctx, SUNB_ILL_INPUT, "y is NULL");
+    const size_t ny = (size_t)ctx->C * ctx->N + (size_t)ctx->Cc;
+    const size_t nc = (size_t)(ctx->C + ctx->Cc);
+    if (!ctx->d_ybuf) {
+        if (cudaMalloc(&ctx->d_ybuf, 8 * ny) != cudaSuccess || cudaMalloc(&ctx->d_sbuf, 4 * nc) != cudaSuccess)
+            return fail(ctx, SUNB_MEM_FAIL, "cudaMalloc staging buffer");
+    }
+    CU(cudaMemcpyAsync(ctx->d_ybuf, host_y, 8 * ny, cudaMemcpyHostToDevice, ctx->stream));
+    int rc = sunb_integrate(ctx, ctx->d_ybuf, t0, tout, host_status ? ctx->d_sbuf : nullptr);
+    if (rc != SUNB_SUCCESS) return rc;
+    CU(cudaMemcpyAsync(host_y, ctx->d_ybuf, 8 * ny, cudaMemcpyDeviceToHost, ctx->stream));
+    if (host_status)
+        CU(cudaMemcpyAsync(host_status, ctx->d_sbuf, 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
+    return sunb_get_totals(ctx, nullptr, nullptr);
+}
+
+int sunb_rhs(sunb_ctx *ctx, const double *dev_y, double *dev_f, int64_t n_cells)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_y || !dev_f || n_cells < 0) return fail(ctx, SUNB_ILL_INPUT, "bad rhs arguments");
+    if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
+    if (ctx->kind == SUNB_MIXED) return fail(ctx, SUNB_ILL_INPUT, "rhs is per kind; use a single-kind context");
+    if (n_cells == 0) return SUNB_SUCCESS;
+    if (ctx->kind == SUNB_MECHANISM) {
+        MechArgs a = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
+        a.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
+        a.cells_per_cta = 4;
+        const int bytes = ctx->off.bytes + 4 * a.lay.bytes;
+        CU(cudaFuncSetAttribute((void *)mech_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        const int grid = (int)std::min<long long>((n_cells + 3) / 4, 8LL * ctx->num_sms);
+        mech_eval_kernel<<<grid, 128, bytes, ctx->stream>>>(a, dev_y, dev_f, n_cells, 0);
+    } else {
+        ThreadArgs a = thread_args(ctx, nullptr, 0.0, 0.0, nullptr);
+        const int grid = (int)std::min<long long>((n_cells + 127) / 128, 8LL * ctx->num_sms);
+        if (ctx->kind == SUNB_ROBERTSON) thread_eval_kernel<RobertsonProblem><<<grid, 128, 0, ctx->stream>>>(a, dev_y, dev_f, n_cells, 0);
+        else thread_eval_kernel<CosmologyProblem><<<grid, 128, 0, ctx->stream>>>(a, dev_y, dev_f, n_cells, 0);
+    }
+    CU(cudaGetLastError());
+    ctx->launches++;
+    return SUNB_SUCCESS;
+}
+
+int sunb_jac(sunb_ctx *ctx, const double *dev_y, double *dev_J, int64_t n_cells)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_y || !dev_J || n_cells < 0) return fail(ctx, SUNB_ILL_INPUT, "bad jac arguments");
+    if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
+    if (ctx->kind == SUNB_MIXED) return fail(ctx, SUNB_ILL_INPUT, "jac is per kind; use a single-kind context");
+    if (n_cells == 0) return SUNB_SUCCESS;
+    if (ctx->kind == SUNB_MECHANISM) {
+        MechArgs a = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
+        a.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
+        a.cells_per_cta = 4;
+        const int bytes = ctx->off.bytes + 4 * a.lay.bytes;
+        CU(cudaFuncSetAttribute((void *)mech_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        const int grid = (int)std::min<long long>((n_cells + 3) / 4, 8LL * ctx->num_sms);
+        mech_eval_kernel<<<grid, 128, bytes, ctx->stream>>>(a, dev_y, dev_J, n_cells, 1);
+    } else {
+        ThreadArgs a = thread_args(ctx, nullptr, 0.0, 0.0, nullptr);
+        const int grid = (int)std::min<long long>((n_cells + 127) / 128, 8LL * ctx->num_sms);
+        if (ctx->kind == SUNB_ROBERTSON) thread_eval_kernel<RobertsonProblem><<<grid, 128, 0, ctx->stream>>>(a, dev_y, dev_J, n_cells, 1);
+        else thread_eval_kernel<CosmologyProblem><<<grid, 128, 0, ctx->stream>>>(a, dev_y, dev_J, n_cells, 1);
+    }
+    CU(cudaGetLastError());
+    ctx->launches++;
+    return SUNB_SUCCESS;
+}
+
+int sunb_lu_solve_batched(int32_t n, int64_t batch, double *dev_A, int32_t *dev_piv, double *dev_b,
+                          int32_t *dev_info, void *stream)
+{
+    return lu_batched<double>(n, batch, dev_A, dev_piv, dev_b, dev_info, stream);
+}
+
+int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *dev_piv, float *dev_b,
+                              int32_t *dev_info, void *stream)
+{
+    return lu_batched<float>(n, batch, dev_A, dev_piv, dev_b, dev_info, stream);
+}
+
+int sunb_get_lanes_per_cell(const sunb_ctx *ctx) { return ctx ? ctx->L : 0; }
+
+int sunb_get_mapping(const sunb_ctx *ctx, int32_t *lanes_per_cell, int32_t *cells_per_cta,
+                     int32_t *ctas_per_sm, float *trial_ms)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (lanes_per_cell) *lanes_per_cell = ctx->L;
+    if (cells_per_cta) *cells_per_cta = ctx->cells_per_cta;
+    if (ctas_per_sm) *ctas_per_sm = ctx->ctas_per_sm;
+    if (trial_ms)
+        for (int i = 0; i < 6; ++i) trial_ms[i] = ctx->tune_ms[i / 2][i % 2];
+    return SUNB_SUCCESS;
+}
+
+int64_t sunb_get_launch_count(const sunb_ctx *ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,69 @@
+// Shared definitions of the batched BDF integrator's CUDA path (sm_103a).
+//
+// Method: arXiv 2405.01713 (Balos et al.), Sec. 2 - every cell's ODE
+// y' = f(t, y; p) is advanced by an adaptive-order (1..5), adaptive-step BDF
+// method with the WRMS error test (Eq. wrms) and a modified Newton iteration
+// stopped by Eq. stop_newton (c_eps = 0.1, c_r = 0.3) on I - gamma J with a
+// dense Jacobian and a pivoted LU (Table 1 approach 2A; Sec. 4.1.4, 4.1.6).
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace sunb {
+
+constexpr int QMAX = 5;
+constexpr int NVEC = 12;            // per-cell vectors held by the controller
+
+// physical constants (CODATA values; cgs units, Ea in cal/mol)
+constexpr double RU = 8.314462618e7;
+constexpr double RC = 1.98720425864083;
+constexpr double PATM = 1013250.0;
+constexpr double LN1E4 = 9.210340371976184;
+
+// Step-control constants.  The paper fixes c_eps = 0.1 and c_r = 0.3
+// (Eq. stop_newton); the rest are readings of points it leaves open:
+// growth limits, failure factors, biases and the rebuild policy.
+constexpr double NLS_COEF = 0.1;       // c_eps
+constexpr double CRDOWN = 0.3;         // c_r
+constexpr double RDIV = 2.0;           // divergence ratio of successive corrections
+constexpr int MAXCOR = 3;              // Newton iterations per attempt
+constexpr int MXNEF = 7;               // error-test failures per step
+constexpr int MXNEF1 = 3;              // failures before the order-1 restart
+constexpr int MXNCF = 10;              // Newton failures per step
+constexpr int MSBP = 20;               // steps between matrix rebuilds
+constexpr double DGMAX = 0.3;          // |gamma/gamma_M - 1| that forces a rebuild
+constexpr double ETA_CF = 0.25;        // step factor after a Newton failure
+constexpr double ETA_MIN_EF = 0.1;     // error-test failure factor bounds
+constexpr double ETA_MAX_EF = 0.9;
+constexpr double ETA_THRESH = 1.5;     // below this the step is kept
+constexpr double ETA_MAX_FIRST = 1e4;  // growth cap after the first step
+constexpr double ETA_MAX = 10.0;       // growth cap afterwards
+constexpr double BIAS_QM1 = 6.0, BIAS_Q = 6.0, BIAS_QP1 = 10.0;
+
+enum Status : int32_t {
+    ST_SUCCESS = 0, ST_TOO_MUCH_WORK = -1, ST_ERR_FAILURE = -3,
+    ST_CONV_FAILURE = -4, ST_H_TOO_SMALL = -5, ST_NONFINITE = -6
+};
+
+// per-cell counters, in the order of the public [C, 8] statistics array
+struct CellStats {
+    int32_t nst, nfe, nje, nni, ncf, nef, qlast, status;
+};
+
+// Integration controls shared by every cell of a launch.
+struct Controls {
+    double rtol;
+    double t0, tout;
+    int32_t max_steps;
+    int32_t max_order;
+};
+
+// Vector slots of the controller.
+enum Vec : int {
+    V_Z0 = 0, V_Z1 = 1,  // Nordsieck columns 0..5 occupy slots 0..5
+    V_ACOR = 6, V_Y = 7, V_F = 8, V_W = 9, V_DEL = 10, V_KS = 11
+};
+
+__device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+}  // namespace sunb

@@ -6,7 +6,9 @@ Sec. 3.2, is de/dt = F + rho * (Gamma * (T/1e4)**-0.7 - Lambda(T)), with
 Lambda a piecewise power law through 64 knots log-spaced over T in
 [1e2, 1e9] K.  Knot values are Lambda_i = T_i * 10**s_i with s_i a seeded,
 bounded random walk, so cooling times T/(rho*Lambda) span about nine decades
-over the density range.
+over the density range.  Rates are per second, scaled so that the outer
+step of the workloads, dt = 1e-6 s, spans cooling times from about 1e-4 to
+1e4 steps (the same outer interval as the chemistry cells it is mixed with).
 """
 from dataclasses import dataclass
 import numpy as np
@@ -14,7 +16,8 @@ import numpy as np
 from .rng import Stream
 
 N_KNOTS = 64
-GAMMA_HEAT = 1.0e4
+RATE_SCALE = 1.0e6   # 1/s per unit of the dimensionless rates
+GAMMA_HEAT = 1.0e4 * RATE_SCALE
 
 
 @dataclass
@@ -34,7 +37,7 @@ def make_cooling_table(seed):
         v = min(1.5, max(-1.5, v + steps[i]))
         walk[i] = v
     lnT = log10T * np.log(10.0)
-    lnLam = lnT + walk * np.log(10.0)
+    lnLam = lnT + walk * np.log(10.0) + np.log(RATE_SCALE)
     return CoolingTable(lnT, lnLam, GAMMA_HEAT)
 
 

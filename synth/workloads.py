@@ -64,27 +64,22 @@ def mech54(n_cells=2 ** 20):
 
 
 def mixed(n_cosmo=2 ** 24, n_mech=2 ** 16):
-    """Cosmology cells plus mech22-type cells integrated over one outer step.
-
-    Both kinds use the same outer interval [0, 1e-6] in their own time units
-    (seconds for the mechanism; the cooling table's time unit is chosen so
-    that cooling times span ~1e-4 .. 1e4 outer steps when dt = 1).
-    """
+    """Cosmology cells plus mech22-type cells integrated over one outer step
+    of 1e-6 s (cosmology cells first in the state and parameter arrays)."""
     table = cooling_table()
     e0, cp = cosmology_cells(n_cosmo, seed=4)
     mech = mech22_mechanism()
     y0, P = mechanism_cells(mech, n_mech, seed=44)
     return dict(name="mixed", kind="mixed", table=table, mech=mech,
                 n_cosmo=n_cosmo, n_mech=n_mech, e0=e0, cosmo_params=cp,
-                y0_mech=y0, mech_params=P, t0=0.0, tout_cosmo=1.0,
-                tout_mech=1.0e-6, rtol=RTOL, atol=ATOL)
+                y0_mech=y0, mech_params=P, t0=0.0, tout=1.0e-6, rtol=RTOL, atol=ATOL)
 
 
 def cosmology(n_cells):
     table = cooling_table()
     e0, cp = cosmology_cells(n_cells, seed=4)
     return dict(name="cosmology", kind="cosmology", table=table, n_cells=n_cells,
-                n_vars=1, y0=e0, params=cp, t0=0.0, tout=1.0, rtol=RTOL,
+                n_vars=1, y0=e0, params=cp, t0=0.0, tout=1.0e-6, rtol=RTOL,
                 atol=ATOL)
 
 

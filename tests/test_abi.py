@@ -1,0 +1,57 @@
+"""The C ABI library loads and exports every entry point that include/sunb.h
+declares; argument validation that needs no GPU (CPU-only checks)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    txt = open(os.path.join(ROOT, "include", "sunb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    return sorted(set(re.findall(r"\b(sunb_[a-z0-9_]+)\s*\(", txt)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2405_01713_b300 import build
+    build.build()
+    import paper_2405_01713_b300 as sb
+    return sb.lib()
+
+
+def test_header_declares_the_boundary():
+    names = _declared()
+    for n in ("sunb_create", "sunb_set_tolerances", "sunb_set_params", "sunb_integrate",
+              "sunb_get_totals", "sunb_rhs", "sunb_jac", "sunb_lu_solve_batched", "sunb_destroy"):
+        assert n in names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in _declared():
+        assert hasattr(lib, n), n
+
+
+def test_binding_covers_every_declared_symbol():
+    import paper_2405_01713_b300 as sb
+    assert set(_declared()) <= set(sb.SIGNATURES)
+
+
+def test_version_and_null_arguments_without_gpu(lib):
+    import paper_2405_01713_b300 as sb
+    assert b"sm_103a" in lib.sunb_version()
+    out = ctypes.c_void_p()
+    assert lib.sunb_create(None, None, ctypes.byref(out)) == sb.ILL_INPUT
+    assert out.value is None
+    assert b"NULL" in lib.sunb_last_error(None)
+    assert lib.sunb_lu_solve_batched(0, 1, None, None, None, None, None) == sb.ILL_INPUT
+    assert lib.sunb_lu_solve_batched(65, 1, None, None, None, None, None) == sb.ILL_INPUT
+    assert lib.sunb_destroy(None) == 0
+
+
+def test_library_is_built_for_sm_103a():
+    from paper_2405_01713_b300 import build
+    assert "arch=compute_103a,code=sm_103a" in build.FLAGS

@@ -1,0 +1,258 @@
+"""GPU parity of the whole integration (steps a1-a15 of the hot path)
+through the C ABI, against the CPU oracle and closed forms.
+
+Parity bars.  The method controls local, not global, error (Sec. 2,
+Eq. wrms), and the oracle and the CUDA path take rounding-level different
+step sequences (the error estimate is a difference of nearly equal values,
+so step-size decisions amplify rounding), so results are compared:
+ * with closed forms on well-conditioned problems, within 10 rtol (the
+   tolerance stated for this path) and tighter at tight rtol;
+ * with the tight-tolerance oracle (rtol 1e-12, the ground truth), where the
+   GPU's error distribution (in units of rtol|y| + atol) must match the
+   oracle's own at the same rtol;
+ * exactly, for invariants (mass conservation) and for integer outcomes
+   (statuses, counters).
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev, need_gpu, quantiles, run_gpu, sb, tol_err, torch
+
+pytestmark = pytest.mark.gpu
+RTOL, ATOL = 1e-6, 1e-10
+
+
+def _oracle_runs(w, cells=None):
+    pb = oracle.problem_from_workload(w, cells=cells)
+    y0 = w["y0"] if cells is None else w["y0"][cells]
+    ym, sm, _, _ = oracle.integrate(pb, y0, w["t0"], w["tout"], RTOL, ATOL)
+    yt, _, _, _ = oracle.integrate(pb, y0, w["t0"], w["tout"], 1e-12, 1e-14)
+    return ym, sm, yt
+
+
+def _assert_matches_method(yg, ym, yt, factor=3.0, floor=10.0):
+    eg = tol_err(yg, yt, RTOL, ATOL)
+    eo = tol_err(ym, yt, RTOL, ATOL)
+    qg, qo = quantiles(eg), quantiles(eo)
+    assert qg["max"] <= factor * qo["max"] + floor, (qg, qo)
+    assert qg["p99"] <= factor * qo["p99"] + floor, (qg, qo)
+    assert qg["median"] <= factor * qo["median"] + 1.0, (qg, qo)
+    return qg, qo
+
+
+def test_robertson_full_config():
+    """1024 cells, t 0 -> 1e5 (the configuration the oracle runs in seconds)."""
+    need_gpu()
+    w = synth.workloads.robertson(1024)
+    yg, cs, tot, _ = run_gpu(w)
+    assert tot["worst_status"] == 0 and np.all(cs[:, 7] == 0)
+    assert np.max(np.abs(yg.sum(axis=1) - 1.0)) < 1e-9
+    ym, sm, yt = _oracle_runs(w)
+    qg, qo = _assert_matches_method(yg, ym, yt)
+    # the method's global error on Robertson stays within ~30 tolerances
+    assert qg["max"] < 60
+    # work counters agree with the oracle's statistically
+    assert abs(cs[:, 0].mean() - sm[:, 0].mean()) < 0.05 * sm[:, 0].mean()
+
+
+@pytest.mark.parametrize("lanes,precision", [(32, 0), (16, 0), (8, 0), (32, 1), (16, 1), (8, 1)])
+def test_mechanism22_mappings_and_precisions(lanes, precision):
+    """Every lanes-per-cell mapping and both matrix precisions solve the
+    same problem to the method's accuracy; the FP32 Newton matrix only
+    changes the iteration, not the error control (spec mixed form)."""
+    need_gpu()
+    w = synth.workloads.mech22(97)
+    yg, cs, tot, it = run_gpu(w, lanes=lanes, precision=precision, max_steps=20000)
+    assert it.lanes_per_cell == lanes
+    assert tot["worst_status"] == 0
+    K = w["mech"].n_species
+    # FP64 Newton corrections conserve mass to rounding; FP32 ones only to the
+    # Newton tolerance, which the FP64 residual iteration keeps below rtol
+    mass_bar = 1e-12 if precision == 0 else 10 * RTOL
+    assert np.max(np.abs(yg[:, :K].sum(axis=1) - 1.0)) < mass_bar
+    ym, sm, yt = _oracle_runs(w)
+    _assert_matches_method(yg, ym, yt)
+
+
+def test_mechanism54_sample():
+    need_gpu()
+    w = synth.workloads.mech54(24)
+    for precision in (0, 1):
+        yg, cs, tot, _ = run_gpu(w, precision=precision, max_steps=20000)
+        assert tot["worst_status"] == 0
+        mass_bar = 1e-12 if precision == 0 else 10 * RTOL
+        assert np.max(np.abs(yg[:, :53].sum(axis=1) - 1.0)) < mass_bar
+        if precision == 0:
+            ym, sm, yt = _oracle_runs(w)
+        _assert_matches_method(yg, ym, yt)
+
+
+def test_isomerisation_closed_form_on_gpu():
+    """A <=> B relaxes exponentially at kf + kr with T fixed: the GPU path is
+    within 10 rtol of the closed form at rtol 1e-6 and within 1e-9 at 1e-11."""
+    need_gpu()
+    m = sb()
+    mech = synth.special_mechanism("isomer")
+    T = 1500.0
+    kf = np.exp(mech.lnA[0]) * T ** mech.beta[0] * np.exp(-mech.Ea[0] / (1.98720425864083 * T))
+    Kc = np.exp(mech.nasa[1, 6] - mech.nasa[0, 6])
+    kr = kf / Kc
+    yeq = 1.0 / (1.0 + Kc)
+    C = 40
+    ya0 = np.linspace(0.05, 0.95, C)
+    y0 = np.stack([ya0, 1 - ya0, np.full(C, T)], axis=1)
+    tout = 1.7 / (kf + kr)
+    exact = yeq + (ya0 - yeq) * np.exp(-(kf + kr) * tout)
+    for rtol, bound in ((1e-6, 10 * 1e-6), (1e-11, 1e-9)):
+        for lanes in (8, 32):
+            it = m.Integrator(m.MECHANISM, C, mech=mech, lanes_per_cell=lanes)
+            it.set_tolerances(rtol, rtol * 1e-4)
+            it.set_params(dev(np.full((C, 1), synth.P_ATM)))
+            yt = dev(y0)
+            it.integrate(yt, 0.0, tout)
+            y = yt.cpu().numpy()
+            assert np.max(np.abs(y[:, 0] - exact) / np.abs(exact)) < bound
+            assert np.max(np.abs(y[:, 2] - T)) < 1e-9 * T
+
+
+def _straight_table(alpha, lam_at_1e4, gamma_heat):
+    lnT = np.linspace(np.log(1e2), np.log(1e9), 64)
+    return synth.CoolingTable(lnT, np.log(lam_at_1e4) + alpha * (lnT - np.log(1e4)), gamma_heat)
+
+
+def test_cooling_closed_forms_on_gpu():
+    """Power-law cooling, power-law heating and constant forcing have closed
+    forms (Sec. 3.2's de/dt = F + R with R a single power law)."""
+    need_gpu()
+    m = sb()
+    C = 64
+    s = synth.Stream(9, 9)
+    e0 = s.log_uniform(C, 1e5, 1e7)
+    rho = s.log_uniform(C, 0.1, 10.0)
+    t = 2.0
+    cases = []
+    alpha, lam4 = 0.6, 5e3
+    c = lam4 / 1e4 ** alpha
+    ex = (e0 ** (1 - alpha) - (1 - alpha) * rho * c * t) ** (1 / (1 - alpha))
+    cases.append((_straight_table(alpha, lam4, 0.0), np.stack([rho, np.zeros(C)], 1), ex))
+    G = 1e4
+    ex = (e0 ** 1.7 + 1.7 * rho * G * 1e4 ** 0.7 * t) ** (1 / 1.7)
+    cases.append((_straight_table(1.0, 1e-250, G), np.stack([rho, np.zeros(C)], 1), ex))
+    F = s.uniform(C, -1e4, 1e5)
+    cases.append((_straight_table(1.0, 1e-250, 0.0), np.stack([rho, F], 1), e0 + F * t))
+    for tab, P, exact in cases:
+        for rtol, bound in ((1e-6, 10 * 1e-6), (1e-11, 1e-9)):
+            it = m.Integrator(m.COSMOLOGY, C, table=tab)
+            it.set_tolerances(rtol, 1e-3 * rtol)
+            it.set_params(dev(P))
+            yt = dev(e0.reshape(C, 1))
+            it.integrate(yt, 0.0, t)
+            y = yt.cpu().numpy()[:, 0]
+            assert np.max(np.abs(y - exact) / exact) < bound
+
+
+def test_cosmology_workload_sample():
+    need_gpu()
+    w = synth.workloads.cosmology(4096)
+    yg, cs, tot, _ = run_gpu(w)
+    assert tot["worst_status"] == 0
+    ym, sm, yt = _oracle_runs(w)
+    _assert_matches_method(yg, ym, yt)
+    # the uneven-batching workload: step counts spread over two decades
+    assert cs[:, 0].max() / max(1, cs[:, 0].min()) > 100
+
+
+def test_mixed_batch_matches_single_kind_runs():
+    """Cosmology and mechanism cells in one launch give the method's
+    accuracy for each kind (cosmology cells first in the arrays)."""
+    need_gpu()
+    w = synth.workloads.mixed(n_cosmo=3000, n_mech=40)
+    for lanes in (8, 32):
+        yg, cs, tot, _ = run_gpu(w, lanes=lanes)
+        assert tot["worst_status"] == 0
+        wc = synth.workloads.cosmology(3000)
+        ym, _, yt = _oracle_runs(wc)
+        _assert_matches_method(yg[:3000].reshape(-1, 1), ym, yt)
+        wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
+                  t0=0.0, tout=w["tout"])
+        ym, _, yt = _oracle_runs(wm)
+        _assert_matches_method(yg[3000:].reshape(40, -1), ym, yt)
+        assert np.all(cs[:, 7] == 0) and cs.shape[0] == 3040
+
+
+@pytest.mark.parametrize("C", [1, 31, 33, 65])
+@pytest.mark.parametrize("lanes", [8, 16, 32])
+def test_ragged_batches(C, lanes):
+    """Batch sizes that leave partial warps and partial CTAs."""
+    need_gpu()
+    w = synth.workloads.mech22(C)
+    yg, cs, tot, _ = run_gpu(w, lanes=lanes, max_steps=20000)
+    assert cs.shape[0] == C and np.all(cs[:, 7] == 0) and np.all(cs[:, 0] > 10)
+    ym, _, yt = _oracle_runs(w)
+    _assert_matches_method(yg, ym, yt)
+
+
+def test_zero_interval_is_identity_and_repeatable():
+    need_gpu()
+    w = synth.workloads.mech22(40)
+    yg, cs, _, _ = run_gpu(w, t0=1e-6, tout=1e-6)
+    np.testing.assert_array_equal(yg, w["y0"])
+    assert np.all(cs[:, 0] == 0)
+    a, _, _, _ = run_gpu(w, lanes=16)
+    b, _, _, _ = run_gpu(w, lanes=16)
+    np.testing.assert_array_equal(a, b)      # deterministic: same bytes twice
+
+
+def test_step_cap_and_nonfinite_cells_are_reported_per_cell():
+    need_gpu()
+    m = sb()
+    w = synth.workloads.robertson(64)
+    yg, cs, tot, _ = run_gpu(w, max_steps=7)
+    assert np.all(cs[:, 7] == m.TOO_MUCH_WORK) and np.all(cs[:, 0] == 7)
+    assert tot["worst_status"] == m.TOO_MUCH_WORK and tot["n_failed"] == 64
+    w = synth.workloads.mech22(48)
+    P = w["params"].copy()
+    P[5, 0] = np.nan
+    P[17, 0] = np.inf
+    yg, cs, tot, _ = run_gpu(w, params=P, max_steps=20000)
+    bad = {5, 17}
+    for c in range(48):
+        assert cs[c, 7] == (m.NONFINITE if c in bad else 0), c
+    assert tot["n_failed"] == 2
+    ym, _, yt = _oracle_runs(w, cells=[0, 1, 2])
+    _assert_matches_method(yg[:3], ym, yt)
+
+
+def test_invalid_arguments_are_rejected_before_launch():
+    need_gpu()
+    m = sb()
+    w = synth.workloads.robertson(8)
+    it = m.from_workload(w)
+    y = dev(w["y0"])
+    with pytest.raises(m.SunbError) as e:
+        it.integrate(y, 0.0, 1.0)            # parameters not set
+    assert e.value.code == m.ILL_INPUT
+    it.set_params(dev(w["params"]))
+    with pytest.raises(m.SunbError):
+        it.integrate(y, 1.0, 0.0)            # tout < t0
+    with pytest.raises(m.SunbError):
+        it.set_tolerances(0.0, 1e-10)
+    with pytest.raises(m.SunbError):
+        m.Integrator(m.ROBERTSON, 0)         # no cells
+    np.testing.assert_array_equal(y.cpu().numpy(), w["y0"])
+
+
+def test_host_entry_point_matches_device_entry_point():
+    need_gpu()
+    m = sb()
+    w = synth.workloads.mech22(64)
+    yd, _, _, _ = run_gpu(w, lanes=16)
+    it = m.from_workload(w, lanes_per_cell=16)
+    it.set_params(dev(w["params"]))
+    yh = w["y0"].copy()
+    st = np.zeros(64, dtype=np.int32)
+    worst = it.integrate_host(yh, 0.0, w["tout"], st)
+    assert worst == 0 and np.all(st == 0)
+    np.testing.assert_array_equal(yh, yd)

@@ -1,0 +1,150 @@
+"""GPU parity of the single steps of the hot path, through the C ABI:
+right-hand side (step a5, Eq. chemODE / nyxODE), analytic Jacobian (a6,
+Table 1 approach 2A) and the batched pivoted LU (a7, Sec. 4.1.6), against
+the CPU oracle (complex-step Jacobian, plain LU)."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from gpu_util import dev, need_gpu, sb, torch
+
+pytestmark = pytest.mark.gpu
+
+
+def _random_states(w, n, seed):
+    """Perturbed workload states: T scaled by [0.8, 1.3], Y by [0.5, 2]."""
+    s = synth.Stream(seed, 77)
+    y = w["y0"][:n].copy()
+    K = w["mech"].n_species
+    y[:, :K] *= s.uniform(n * K, 0.5, 2.0).reshape(n, K)
+    y[:, K] *= s.uniform(n, 0.8, 1.3)
+    return y
+
+
+@pytest.mark.parametrize("name", ["mech22", "mech54"])
+def test_mechanism_rhs_matches_oracle(name):
+    need_gpu()
+    w = getattr(synth.workloads, name)(67)
+    y = _random_states(w, 67, 1)
+    it = sb().from_workload(w)
+    it.set_params(dev(w["params"]))
+    f = it.rhs(dev(y)).cpu().numpy()
+    pb = oracle.problem_from_workload(w)
+    for c in range(67):
+        fo = oracle.rhs(pb, y[c], c)
+        scale = np.abs(fo).max()
+        assert np.max(np.abs(f[c] - fo)) <= 1e-12 * scale, c
+
+
+@pytest.mark.parametrize("name", ["mech22", "mech54"])
+def test_mechanism_analytic_jacobian_matches_complex_step(name):
+    need_gpu()
+    w = getattr(synth.workloads, name)(35)
+    y = _random_states(w, 35, 2)
+    it = sb().from_workload(w)
+    it.set_params(dev(w["params"]))
+    J = it.jac(dev(y)).cpu().numpy()
+    pb = oracle.problem_from_workload(w)
+    for c in range(35):
+        Jo = oracle.jac(pb, y[c], c, mode=0)
+        scale = np.abs(Jo).max(axis=1, keepdims=True) + 1e-300
+        assert np.max(np.abs(J[c] - Jo) / scale) < 1e-8, c
+
+
+def test_special_mechanism_jacobian_is_exact():
+    """Isomerisation A <=> B: the Y block of J is the rate matrix."""
+    need_gpu()
+    mech = synth.special_mechanism("isomer")
+    m = sb()
+    it = m.Integrator(m.MECHANISM, 1, mech=mech)
+    it.set_params(dev(np.array([[synth.P_ATM]])))
+    T = 1300.0
+    J = it.jac(dev(np.array([[0.6, 0.4, T]])))[0].cpu().numpy()
+    kf = np.exp(mech.lnA[0]) * T ** mech.beta[0] * np.exp(-mech.Ea[0] / (1.98720425864083 * T))
+    kr = kf / np.exp(mech.nasa[1, 6] - mech.nasa[0, 6])
+    np.testing.assert_allclose(J[:2, :2], [[-kf, kr], [kf, -kr]], rtol=1e-12)
+
+
+def test_robertson_and_cosmology_rhs_jac():
+    need_gpu()
+    m = sb()
+    w = synth.workloads.robertson(33)
+    s = synth.Stream(3, 3)
+    y = np.abs(s.normal(33 * 3).reshape(33, 3)) * np.array([1.0, 1e-5, 1.0])
+    it = m.from_workload(w)
+    it.set_params(dev(w["params"]))
+    pb = oracle.problem_from_workload(w)
+    f = it.rhs(dev(y)).cpu().numpy()
+    J = it.jac(dev(y)).cpu().numpy()
+    for c in range(33):
+        np.testing.assert_allclose(f[c], oracle.rhs(pb, y[c], c), rtol=1e-13, atol=1e-20)
+        np.testing.assert_allclose(J[c], oracle.jac(pb, y[c], c), rtol=1e-13, atol=1e-20)
+    w = synth.workloads.cosmology(129)
+    e = np.exp(s.uniform(129, np.log(0.5), np.log(3e9))).reshape(129, 1)   # spans floor and both ends
+    it = m.from_workload(w)
+    it.set_params(dev(w["params"]))
+    pb = oracle.problem_from_workload(w)
+    f = it.rhs(dev(e)).cpu().numpy()
+    J = it.jac(dev(e)).cpu().numpy()
+    for c in range(129):
+        fo = oracle.rhs(pb, e[c], c)
+        Jo = oracle.jac(pb, e[c], c)
+        np.testing.assert_allclose(f[c], fo, rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(J[c], Jo, rtol=1e-12, atol=1e-300)
+
+
+@pytest.mark.parametrize("n", [1, 3, 22, 33, 54, 64])
+def test_batched_lu_matches_oracle(n):
+    """Pivot sequences bit-exact; factors and solutions to rounding."""
+    need_gpu()
+    m = sb()
+    B = 37
+    s = synth.Stream(n, 11)
+    A = s.normal(B * n * n).reshape(B, n, n)
+    A[1] = np.diag(np.arange(1, n + 1, dtype=float))        # no exchanges
+    if n > 2:
+        A[2, :, 0] = 0.0
+        A[2, -1, 0] = 1.0                                    # forced exchange with the last row
+    b = s.normal(B * n).reshape(B, n)
+    At, bt = dev(A), dev(b)
+    piv, info = m.lu_solve_batched(At, bt)
+    LU, piv, x, info = At.cpu().numpy(), piv.cpu().numpy(), bt.cpu().numpy(), info.cpu().numpy()
+    assert np.all(info == 0)
+    for i in range(B):
+        LUo, pivo, _ = oracle.lu_factor(A[i])
+        np.testing.assert_array_equal(piv[i], pivo)
+        np.testing.assert_allclose(LU[i], LUo, rtol=1e-12, atol=1e-12 * np.abs(A[i]).max())
+        np.testing.assert_allclose(x[i], oracle.lu_solve(LUo, pivo, b[i]), rtol=1e-10, atol=1e-11)
+
+
+def test_batched_lu_fp32_and_singular_info():
+    need_gpu()
+    m = sb()
+    n, B = 22, 16
+    s = synth.Stream(5, 12)
+    A = s.normal(B * n * n).reshape(B, n, n) + 4 * np.eye(n)
+    A[3, :, 5] = 0.0                     # singular: column 5 has no pivot
+    b = s.normal(B * n).reshape(B, n)
+    At = torch.tensor(A, dtype=torch.float32, device="cuda")
+    bt = torch.tensor(b, dtype=torch.float32, device="cuda")
+    piv, info = m.lu_solve_batched(At, bt)
+    info = info.cpu().numpy()
+    assert info[3] == 6
+    assert np.all(np.delete(info, 3) == 0)
+    x = bt.cpu().numpy()
+    for i in range(B):
+        if i == 3:
+            continue
+        xr = np.linalg.solve(A[i], b[i])
+        assert np.max(np.abs(x[i] - xr)) < 1e-4 * np.max(np.abs(xr))
+
+
+def test_lu_rejects_bad_sizes():
+    need_gpu()
+    m = sb()
+    A = torch.zeros((2, 65, 65), dtype=torch.float64, device="cuda")
+    b = torch.zeros((2, 65), dtype=torch.float64, device="cuda")
+    with pytest.raises(m.SunbError) as e:
+        m.lu_solve_batched(A, b)
+    assert e.value.code == m.ILL_INPUT
