@@ -133,20 +133,25 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- workloads
-def make_workload(name):
+def make_workload(name, cells=None):
+    """The named workload at full size, or its first ``cells`` cells (for
+    small profiling cases; prefix-compatible with the full batch)."""
+    kw = {} if cells is None else {"n_cells": cells}
     if name == "mech22":
-        return synth.workloads.mech22()
+        return synth.workloads.mech22(**kw)
     if name == "mech54":
-        return synth.workloads.mech54()
+        return synth.workloads.mech54(**kw)
     if name == "robertson":
-        return synth.workloads.robertson()
+        return synth.workloads.robertson(**kw)
     if name == "mixed":
-        return synth.workloads.mixed()
+        return synth.workloads.mixed() if cells is None else \
+            synth.workloads.mixed(n_cosmo=cells * 256, n_mech=cells)
     if name == "cosmology":
-        return synth.workloads.cosmology(2 ** 24)
+        return synth.workloads.cosmology(2 ** 24 if cells is None else cells)
     raise ValueError(name)
 
 
+LANES_OVERRIDE = 0
 FORMS = {
     "plain": dict(precision=0, lanes_per_cell=32, schedule=1),
     "chosen": dict(precision=1, lanes_per_cell=0, schedule=0),
@@ -165,7 +170,9 @@ def flat_inputs(w):
 
 def make_integrator(w, form):
     import paper_2405_01713_b300 as sb
-    kw = FORMS[form]
+    kw = dict(FORMS[form])
+    if form == "chosen" and LANES_OVERRIDE:
+        kw["lanes_per_cell"] = LANES_OVERRIDE
     prec = kw["precision"] if w["kind"] in ("mechanism", "mixed") else 0
     return sb.from_workload(w, precision=prec, lanes_per_cell=kw["lanes_per_cell"],
                             schedule=kw["schedule"])
@@ -275,16 +282,23 @@ def main():
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cells", type=int, default=None,
+                    help="first N cells only (small profiling cases; not a bench value)")
+    ap.add_argument("--lanes", type=int, default=0, help="fix the chosen form's lanes per cell")
     args = ap.parse_args()
+    global LANES_OVERRIDE
+    LANES_OVERRIDE = args.lanes
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    w = make_workload(args.workload)
+    w = make_workload(args.workload, args.cells)
     workload_name = {"mech22": "mech22: 21 species + T, 84 reactions, 2^18 cells, dt 1e-6 s",
                      "mech54": "mech54: 53 species + T, 270 reactions, 2^20 cells, dt 1e-6 s",
                      "mixed": "mixed: 2^24 cosmology cells + 2^16 mech22 cells, dt 1e-6 s",
                      "robertson": "robertson: 1024 cells, t 0 -> 1e5",
                      "cosmology": "cosmology: 2^24 cells, dt 1e-6 s"}[args.workload]
+    if args.cells is not None:
+        workload_name += f" (first {args.cells} cells only)"
 
     if args.impl == "reference":
         if rank != 0:

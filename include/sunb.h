@@ -173,11 +173,12 @@ int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *d
 int sunb_get_lanes_per_cell(const sunb_ctx *ctx);
 
 /* Mechanism mapping in use: lanes per cell, cells per CTA, CTAs per SM;
- * trial_ms (nullable, 6 floats) receives the autotuner's trial times for
- * L = 8, 16, 32 at two CTA sizes each (0 = not run, -1 = duplicate).  With
- * lanes_per_cell = 0 at create, the first sunb_integrate runs the trials
- * (synchronously, on a scratch copy of the first cells) and keeps the
- * fastest mapping for the context's lifetime. */
+ * trial_ms (nullable, 6 floats) receives, for L = 8, 16, 32 in turn, the
+ * autotuner's trial time in ms and the number of cells of that trial (0 =
+ * not run, -1 = mapping does not fit).  With lanes_per_cell = 0 at create,
+ * the first sunb_integrate runs the trials (synchronously, each on a
+ * scratch copy of eight waves of the first cells) and keeps the mapping
+ * with the least time per cell for the context's lifetime. */
 int sunb_get_mapping(const sunb_ctx *ctx, int32_t *lanes_per_cell, int32_t *cells_per_cta,
                      int32_t *ctas_per_sm, float *trial_ms);
 

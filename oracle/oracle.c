@@ -37,9 +37,12 @@
  *    the first step and 10 afterwards, and at 1 right after a failed attempt;
  *    order changes considered after q+1 steps at the current order;
  *  - error-test failure: eta in [0.1, 0.9], lower order when that allows a
- *    larger step; from the third failure of a step, eta = 0.1 and a restart
- *    at order 1; seven failures end the cell (ERR_FAILURE); Newton failure:
- *    eta = 0.25, ten per step end the cell (CONV_FAILURE);
+ *    larger step; from the third failure of a step, eta = 0.1 at order 1,
+ *    reached by lowering the order of the interpolating polynomial (its
+ *    slope then comes from accepted states, not from f at a state that may
+ *    sit slightly off a stiff slow manifold); seven failures end the cell
+ *    (ERR_FAILURE); Newton failure: eta = 0.25, ten per step end the cell
+ *    (CONV_FAILURE);
  *  - first step from the starting-step algorithm of Hairer, Norsett and
  *    Wanner (Solving ODEs I, Sec. II.4) with the WRMS norm;
  *  - every call is a cold start at order 1 and lands exactly on tout.
@@ -415,14 +418,17 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                 }
                 h *= eta; rescale(q, n, z, eta);
             } else {
+                /* from the third failure: order 1 and eta = 0.1; the order
+                 * is lowered through the interpolating polynomials, which
+                 * keeps the line through the last two accepted states */
                 eta = 0.1;
-                h *= eta;
-                rhs_r(pb, cell, z, f);
-                s.nfe++;
-                for (int j = 2; j <= QMAX; ++j) for (int i = 0; i < n; ++i) z[j * n + i] = 0.0;
-                for (int i = 0; i < n; ++i) z[n + i] = h * f[i];
-                for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
-                q = 1; qwait = 2; have_ksave = 0;
+                if (q > 1) {
+                    double nodes[QMAX], sacc = 0.0;
+                    for (int i = 0; i < q - 1; ++i) { sacc += hist[i]; nodes[i] = sacc / h; }
+                    for (; q > 1; --q) orc_order_decrease(q, n, z, nodes);
+                }
+                h *= eta; rescale(q, n, z, eta);
+                qwait = 2; have_ksave = 0;
             }
             etamax = 1.0; last = 0;
             if (t + h == t) { s.status = ORC_H_TOO_SMALL; break; }

@@ -24,7 +24,8 @@
 //    orders q-1/q/q+1, threshold 1.5, caps 1e4 (first step) / 10 / 1
 //    (after a failure); order change considered after q+1 steps at q;
 //  * failures: error test -> eta in [0.1, 0.9] (or order q-1), third
-//    failure -> eta 0.1 and order-1 restart, seventh -> ERR_FAILURE;
+//    failure -> eta 0.1 at order 1 (reached by lowering the order of the
+//    interpolating polynomial), seventh -> ERR_FAILURE;
 //    Newton -> eta 0.25, tenth -> CONV_FAILURE;
 //  * first step by the Hairer-Norsett-Wanner starting-step algorithm;
 //  * each call is a cold start at order 1 that lands exactly on tout.
@@ -94,6 +95,32 @@ __device__ __forceinline__ void decrease_coeffs(int q, const double *nodes, doub
     }
 }
 
+// Equal-step coefficients (xi_i = i): l = coefficients of prod (1 + x/i),
+// the classical fixed-step Nordsieck BDF vectors.  Used whenever the last q
+// steps had the current size, so the coefficients need no divisions.
+__constant__ double GEAR_L[QMAX + 1][QMAX + 1] = {
+    {1.0, 0, 0, 0, 0, 0},
+    {1.0, 1.0, 0, 0, 0, 0},
+    {1.0, 3.0 / 2.0, 1.0 / 2.0, 0, 0, 0},
+    {1.0, 11.0 / 6.0, 1.0, 1.0 / 6.0, 0, 0},
+    {1.0, 25.0 / 12.0, 35.0 / 24.0, 5.0 / 12.0, 1.0 / 24.0, 0},
+    {1.0, 137.0 / 60.0, 15.0 / 8.0, 17.0 / 24.0, 1.0 / 8.0, 1.0 / 120.0}};
+
+__constant__ double GEAR_INV[QMAX + 1] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0};
+// 1/l_1 = 1/H_q (H_q harmonic numbers) and C_q = 1/(1 + H_q (q+1))
+__constant__ double GEAR_IL1[QMAX + 1] = {1.0, 1.0, 2.0 / 3.0, 6.0 / 11.0, 12.0 / 25.0, 60.0 / 137.0};
+__constant__ double GEAR_CQ[QMAX + 1] = {1.0, 1.0 / 3.0, 2.0 / 11.0, 6.0 / 50.0, 12.0 / 137.0, 60.0 / 882.0};
+
+// eta_p >= 1.5 exactly when bias^2 * ||E_p||^2 <= (2/3 - 1e-6)^(2(p+1)):
+// the step-size choice takes the power only when a change can follow.
+__device__ __forceinline__ double eta_viable2(int p)
+{
+    const double b = 2.0 / 3.0 - 1e-6;
+    double r = 1.0;
+    for (int i = 0; i < 2 * (p + 1); ++i) r *= b;
+    return r;
+}
+
 template <class C>
 __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
 {
@@ -140,6 +167,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
 #pragma unroll
     for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
     double gamma_M = 0.0, etamax = ETA_MAX_FIRST, h_ks = 0.0;
+    int nsame = 0;    // leading entries of hist equal to the current h
 
     while (t < tout) {
         if (s.nst >= ctl.max_steps) { s.status = ST_TOO_MUCH_WORK; break; }
@@ -149,16 +177,30 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
             c.rescale(q, hn * rcp(h));
             h = hn;
             last = 1;
+            nsame = 0;
         }
         c.set_weights(V_Z0, ctl.rtol);          // Eq. wrms: weights from y^{n-1}
         int ncf = 0, nef = 0;
         double dsm2 = 0.0, l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1], Cq = 0.0;
         for (;;) {   // attempts
             c.predict(q);
-            bdf_xi(q + 1, h, hist, xi, inv);
-            bdf_l(q, inv, l);
-            const double l1 = l[1], il1 = rcp(l1), gamma = h * il1;
-            Cq = rcp(1.0 + l1 * xi[q]);
+            double il1;
+            if (nsame >= q) {
+#pragma unroll
+                for (int i = 0; i <= QMAX; ++i) {
+                    xi[i] = (double)(i + 1);
+                    inv[i] = GEAR_INV[i];
+                    l[i] = GEAR_L[q][i];
+                }
+                il1 = GEAR_IL1[q];
+                Cq = GEAR_CQ[q];
+            } else {
+                bdf_xi(q + 1, h, hist, xi, inv);
+                bdf_l(q, inv, l);
+                il1 = rcp(l[1]);
+                Cq = rcp(1.0 + l[1] * xi[q]);
+            }
+            const double gamma = h * il1;
             const double Cq2 = Cq * Cq;
             int fresh = 0, conv = 0, fcur = 0;   // fcur: V_F holds f(z0) already
             if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
@@ -197,7 +239,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 if (ncf >= MXNCF) { s.status = ST_CONV_FAILURE; break; }
                 h *= ETA_CF;
                 c.rescale(q, ETA_CF);
-                force_setup = 1; etamax = 1.0; last = 0;
+                force_setup = 1; etamax = 1.0; last = 0; nsame = 0;
                 if (t + h == t) { s.status = ST_H_TOO_SMALL; break; }
                 continue;
             }
@@ -232,15 +274,26 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 h *= eta;
                 c.rescale(q, eta);
             } else {
+                // third failure on: order 1 through the interpolating
+                // polynomials (keeps the line through the last two accepted
+                // states), eta = 0.1
+                if (q > 1) {
+                    double nodes[QMAX], sacc = 0.0, e[QMAX + 1];
+                    const double rh = rcp(h);
+                    for (int i = 0; i < QMAX; ++i) {
+                        sacc += hist[i];
+                        nodes[i] = sacc * rh;
+                    }
+                    for (; q > 1; --q) {
+                        decrease_coeffs(q, nodes, e);
+                        c.order_decrease(q, e);
+                    }
+                }
                 h *= ETA_MIN_EF;
-                c.rhs(V_Z0, V_F);
-                s.nfe++;
-                c.restart(h);      // z1 = h f, z2.. = 0
-#pragma unroll
-                for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
-                q = 1; qwait = 2; have_ks = 0;
+                c.rescale(q, ETA_MIN_EF);
+                qwait = 2; have_ks = 0;
             }
-            etamax = 1.0; last = 0;
+            etamax = 1.0; last = 0; nsame = 0;
             if (t + h == t) { s.status = ST_H_TOO_SMALL; break; }
         }
         if (s.status != ST_SUCCESS) break;
@@ -256,16 +309,18 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
 
         qwait--;
         const double l1 = l[1];
-        double eta = eta_from(dsm2, q, BIAS_Q);
+        double eta = 1.0;
         int newq = q;
         const double kfac = l1 * l[q] * Cq;     // h^{q+1} y^{(q+1)}/(q+1)! = kfac * Delta
+        if (BIAS_Q * BIAS_Q * dsm2 <= eta_viable2(q)) eta = eta_from(dsm2, q, BIAS_Q);
         if (qwait == 0) {
             double em = 0.0, ep = 0.0;
             if (q > 1) {
                 double l1m = 0.0, pm = 1.0;
                 for (int i = 0; i < q - 1; ++i) { l1m += inv[i]; pm *= xi[i]; }
                 const double f = pm * rcp(l1m);
-                em = eta_from(c.wrms2(q) * f * f, q - 1, BIAS_QM1);
+                const double d2 = c.wrms2(q) * f * f;
+                if (BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1)) em = eta_from(d2, q - 1, BIAS_QM1);
             }
             if (q < qmax && have_ks) {
                 double rq = 1.0;
@@ -275,7 +330,8 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 for (int i = 0; i <= q; ++i) pp *= xi[i];
                 const double l1p = l1 + inv[q];
                 const double f = pp * rcp(l1p * (q + 2));
-                ep = eta_from(c.wrms2_lin(kfac, V_ACOR, -rq, V_KS) * f * f, q + 1, BIAS_QP1);
+                const double d2 = c.wrms2_lin(kfac, V_ACOR, -rq, V_KS) * f * f;
+                if (BIAS_QP1 * BIAS_QP1 * d2 <= eta_viable2(q + 1)) ep = eta_from(d2, q + 1, BIAS_QP1);
             }
             if (em > eta && em >= ep) { eta = em; newq = q - 1; }
             else if (ep > eta) { eta = ep; newq = q + 1; }
@@ -296,6 +352,9 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         if (eta != 1.0) {
             h *= eta;
             c.rescale(q, eta);
+            nsame = 0;
+        } else if (nsame < QMAX) {
+            ++nsame;
         }
         etamax = ETA_MAX;
     }

@@ -37,7 +37,7 @@ namespace sunb {
 struct MechTabOffsets {
     int K, M, N, nnz;
     int invW, W, cpc, hc, sc, dcp, rpar, atol, inc_nu;   // double arrays
-    int ridx, inc_ptr, inc_j;                            // 32-bit arrays
+    int ridx, inc_ptr, inc_j, inc_nuf, invWf;            // 32-bit arrays
     int bytes;                                           // blob size (multiple of 16)
 };
 
@@ -52,7 +52,14 @@ struct MechTab {
     const double *invW, *W, *cpc, *hc, *sc, *dcp, *rpar, *atol, *inc_nu;
     const uint32_t *ridx;
     const int32_t *inc_ptr, *inc_j;
+    const float *inc_nuf, *invWf;          // FP32 copies for the FP32 Newton matrix
+    template <typename T> __device__ __forceinline__ const T *nu() const;
+    template <typename T> __device__ __forceinline__ const T *iw() const;
 };
+template <> __device__ __forceinline__ const double *MechTab::nu<double>() const { return inc_nu; }
+template <> __device__ __forceinline__ const float *MechTab::nu<float>() const { return inc_nuf; }
+template <> __device__ __forceinline__ const double *MechTab::iw<double>() const { return invW; }
+template <> __device__ __forceinline__ const float *MechTab::iw<float>() const { return invWf; }
 
 __device__ __forceinline__ MechTab mech_tab_at(const unsigned char *base, const MechTabOffsets &o)
 {
@@ -70,6 +77,8 @@ __device__ __forceinline__ MechTab mech_tab_at(const unsigned char *base, const 
     t.ridx = reinterpret_cast<const uint32_t *>(base + o.ridx);
     t.inc_ptr = reinterpret_cast<const int32_t *>(base + o.inc_ptr);
     t.inc_j = reinterpret_cast<const int32_t *>(base + o.inc_j);
+    t.inc_nuf = reinterpret_cast<const float *>(base + o.inc_nuf);
+    t.invWf = reinterpret_cast<const float *>(base + o.invWf);
     return t;
 }
 
@@ -188,7 +197,9 @@ struct GroupCell {
     MT *xs;               // [N] solve scratch
     MT *dinv;             // [N] reciprocal pivots
     double *C, *eg, *egi, *hRT, *cpR, *wdot, *u, *wT;   // species scratch ([K+1] for the first three)
-    double *q, *dq, *dqdT;                              // [M], [6M], [M]
+    double *q;                                          // [M]
+    MT *dq;                                             // [6M] gamma dq_j/dC at each position
+    double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
     double *yg;
 
     __device__ __forceinline__ double *V(int s) const { return vec + s * NP; }
@@ -205,8 +216,9 @@ struct GroupCell {
         C = sp; eg = C + (K + 1); egi = eg + (K + 1); hRT = egi + (K + 1);
         cpR = hRT + (K + 1); wdot = cpR + K; u = wdot + K; wT = u + K;
         q = reinterpret_cast<double *>(base + lay.rq);
-        dq = reinterpret_cast<double *>(base + lay.dq);
-        dqdT = dq + 6 * M;
+        dq = reinterpret_cast<MT *>(base + lay.dq);
+        dqdT = reinterpret_cast<double *>(base + lay.dq + ((6 * M * (int)sizeof(MT) + 15) & ~15));
+        uq = dqdT + M;
         if (g.lane == 0) { C[K] = 1.0; eg[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; }
         g.sync();
     }
@@ -429,17 +441,22 @@ struct GroupCell {
             const double fwd = kf * (c0 * c1 * c2), rev = kr * (d0 * d1 * d2);
             q[j] = fwd - rev;
             if (JAC) {
-                double *dj = dq + 6 * j;
+                MT *dj = dq + 6 * j;
                 const double gkf = gamma * kf, gkr = gamma * kr;
-                dj[0] = gkf * (c1 * c2);
-                dj[1] = gkf * (c0 * c2);
-                dj[2] = gkf * (c0 * c1);
-                dj[3] = -gkr * (d1 * d2);
-                dj[4] = -gkr * (d0 * d2);
-                dj[5] = -gkr * (d0 * d1);
+                dj[0] = (MT)(gkf * (c1 * c2));
+                dj[1] = (MT)(gkf * (c0 * c2));
+                dj[2] = (MT)(gkf * (c0 * c1));
+                dj[3] = (MT)(-gkr * (d1 * d2));
+                dj[4] = (MT)(-gkr * (d0 * d2));
+                dj[5] = (MT)(-gkr * (d0 * d1));
                 const double af = rp[1] + rp[2] * invT;
                 const double dH = (hRT[p0] + hRT[p1] + hRT[p2]) - (hRT[r0] + hRT[r1] + hRT[r2]);
-                dqdT[j] = invT * (af * fwd - (af - dH + (double)dnu) * rev);
+                dqdT[j] = gamma * invT * (af * fwd - (af - dH + (double)dnu) * rev);
+                // sum_m C_m dq_j/dC_m = n_r fwd - n_p rev (each product term is
+                // homogeneous in C): formed in FP64 here, because summing the
+                // large, nearly cancelling row entries instead loses it in FP32
+                const int nr = (int)(b >> 24), np = nr + dnu;
+                uq[j] = gamma * ((double)nr * fwd - (double)np * rev);
             }
         }
         g.sync();
@@ -461,29 +478,32 @@ struct GroupCell {
         if (!JAC) return 1;
 
         // ---- Newton matrix M = I - gamma J (gamma folded into dq, dqdT) ----
-        // rows k < K of gamma*Jc, and gamma * dwdot/dT, gamma * u
-        for (int k = g.lane; k < K; k += L) {
-            MT *row = mat + k * N;
-            for (int m = 0; m < N; ++m) row[m] = (MT)0;
-            double wt = 0.0;
-            const int e1 = tb.inc_ptr[k + 1];
-            for (int e = tb.inc_ptr[k]; e < e1; ++e) {
-                const int j = tb.inc_j[e];
-                const double nu = tb.inc_nu[e];
-                const uint32_t a = tb.ridx[2 * j], b = tb.ridx[2 * j + 1];
-                const double *dj = dq + 6 * j;
-                wt += nu * dqdT[j];
-                row[a & 0xff] += (MT)(nu * dj[0]);
-                row[(a >> 8) & 0xff] += (MT)(nu * dj[1]);
-                row[(a >> 16) & 0xff] += (MT)(nu * dj[2]);
-                row[a >> 24] += (MT)(nu * dj[3]);
-                row[b & 0xff] += (MT)(nu * dj[4]);
-                row[(b >> 8) & 0xff] += (MT)(nu * dj[5]);
+        // rows k < K of gamma*Jc (in MT), and gamma * dwdot/dT, gamma * u (in FP64)
+        {
+            const MT *nu = tb.template nu<MT>();
+            for (int k = g.lane; k < K; k += L) {
+                MT *row = mat + k * N;
+                for (int m = 0; m < N; ++m) row[m] = (MT)0;
+                double wt = 0.0, uk = 0.0;
+                const int e1 = tb.inc_ptr[k + 1];
+                for (int e = tb.inc_ptr[k]; e < e1; ++e) {
+                    const int j = tb.inc_j[e];
+                    const MT n = nu[e];
+                    const double nd = tb.inc_nu[e];
+                    const uint32_t a = tb.ridx[2 * j], b = tb.ridx[2 * j + 1];
+                    const MT *dj = dq + 6 * j;
+                    wt += nd * dqdT[j];
+                    uk += nd * uq[j];
+                    row[a & 0xff] += n * dj[0];
+                    row[(a >> 8) & 0xff] += n * dj[1];
+                    row[(a >> 16) & 0xff] += n * dj[2];
+                    row[a >> 24] += n * dj[3];
+                    row[b & 0xff] += n * dj[4];
+                    row[(b >> 8) & 0xff] += n * dj[5];
+                }
+                wT[k] = wt;
+                u[k] = uk;
             }
-            MT uk = (MT)0;
-            for (int m = 0; m < K; ++m) uk += row[m] * (MT)C[m];
-            wT[k] = gamma * wt;
-            u[k] = (double)uk;
         }
         g.sync();
         // scalars of the temperature row
@@ -510,15 +530,18 @@ struct GroupCell {
         const double gJTT = -(gamma * sA1 + T * sA2) * rcp(rho * cpm) - gamma * fT * (-invT + sA3 * icpm);
         g.sync();
         // species rows: gamma*J_kl = (W_k/W_l)(gamma Jc_kl + (Ru T/P) gamma (wdot_k - u_k)), then M = I - gamma J
-        for (int k = g.lane; k < K; k += L) {
-            MT *row = mat + k * N;
-            const double ck = rtP * (gamma * wdot[k] - u[k]);
-            const double Wk = tb.W[k];
-            for (int l = 0; l < K; ++l) {
-                const MT gJ = (MT)(Wk * tb.invW[l]) * (row[l] + (MT)ck);
-                row[l] = ((l == k && add_identity) ? (MT)1 : (MT)0) - gJ;
+        {
+            const MT *iw = tb.template iw<MT>();
+            for (int k = g.lane; k < K; k += L) {
+                MT *row = mat + k * N;
+                const MT ck = (MT)(rtP * (gamma * wdot[k] - u[k]));
+                const MT Wk = (MT)tb.W[k];
+                for (int l = 0; l < K; ++l) {
+                    const MT gJ = (Wk * iw[l]) * (row[l] + ck);
+                    row[l] = ((l == k && add_identity) ? (MT)1 : (MT)0) - gJ;
+                }
+                row[K] = (MT)(-(tb.W[k] * rrho) * (wT[k] + (gamma * wdot[k] - u[k]) * invT));
             }
-            row[K] = (MT)(-(Wk * rrho) * (wT[k] + (gamma * wdot[k] - u[k]) * invT));
         }
         for (int l = g.lane; l < K; l += L) mat[K * N + l] = -xs[l];
         if (g.lane == 0) mat[K * N + K] = (MT)((add_identity ? 1.0 : 0.0) - gJTT);

@@ -103,9 +103,12 @@ __device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const C
 template <int L>
 __device__ __forceinline__ unsigned group_mask()
 {
-    if (L == 32) return 0xffffffffu;
-    const int w = threadIdx.x & 31;
-    return ((1u << L) - 1u) << (w & ~(L - 1));
+    if constexpr (L == 32) {
+        return 0xffffffffu;
+    } else {
+        const int w = threadIdx.x & 31;
+        return ((1u << L) - 1u) << (w & ~(L - 1));
+    }
 }
 
 // Persistent mechanism kernel: L lanes per cell, cells_per_cta cells per
@@ -356,7 +359,7 @@ struct sunb_ctx {
     int32_t *d_sbuf = nullptr;
     double *d_tune = nullptr;        // autotuning sample (copy of the first cells)
     long long tune_cells = 0;
-    float tune_ms[3][2] = {{0}};     // trial times, L = 8/16/32 x two CTA sizes
+    float tune_ms[3][2] = {{0}};     // per L = 8/16/32: trial ms and trial cells
     long long launches = 0;
     std::string err;
 };
@@ -406,7 +409,8 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
         std::stable_partition(ps, ps + 3, [K](int v) { return v != K; });
         const int dnu = np - nr;
         ridx[2 * j] = (uint32_t)rs[0] | ((uint32_t)rs[1] << 8) | ((uint32_t)rs[2] << 16) | ((uint32_t)ps[0] << 24);
-        ridx[2 * j + 1] = (uint32_t)ps[1] | ((uint32_t)ps[2] << 8) | ((uint32_t)(dnu + 8) << 16);
+        ridx[2 * j + 1] = (uint32_t)ps[1] | ((uint32_t)ps[2] << 8) | ((uint32_t)(dnu + 8) << 16) |
+                          ((uint32_t)nr << 24);
         int net[64] = {0};
         for (int s = 0; s < 3; ++s) {
             if (r[s] >= 0) net[r[s]] -= 1;
@@ -426,6 +430,8 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     o.sc = take(8 * 6 * K); o.dcp = take(8 * 4 * K); o.rpar = take(8 * 3 * M); o.atol = take(8 * N);
     o.inc_nu = take(8 * std::max(nnz, 1)); o.ridx = take(4 * 2 * M); o.inc_ptr = take(4 * (K + 1));
     o.inc_j = take(4 * std::max(nnz, 1));
+    o.inc_nuf = take(4 * std::max(nnz, 1));
+    o.invWf = take(4 * K);
     o.bytes = off;
     std::vector<unsigned char> blob(off, 0);
     auto D = [&](int o_) { return reinterpret_cast<double *>(blob.data() + o_); };
@@ -451,7 +457,13 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     int e = 0;
     for (int k = 0; k < K; ++k) {
         I(o.inc_ptr)[k] = e;
-        for (auto &pr : inc[k]) { I(o.inc_j)[e] = pr.first; D(o.inc_nu)[e] = (double)pr.second; ++e; }
+        for (auto &pr : inc[k]) {
+            I(o.inc_j)[e] = pr.first;
+            D(o.inc_nu)[e] = (double)pr.second;
+            reinterpret_cast<float *>(blob.data() + o.inc_nuf)[e] = (float)pr.second;
+            ++e;
+        }
+        reinterpret_cast<float *>(blob.data() + o.invWf)[k] = (float)(1.0 / m->W[k]);
     }
     I(o.inc_ptr)[K] = e;
     std::memcpy(blob.data() + o.ridx, ridx.data(), 4 * 2 * M);
@@ -472,7 +484,7 @@ static CellLayout make_layout(int N, int K, int M, int mt)
     l.xs = take(mt * 2 * N);
     l.sp = take(8 * (4 * (K + 1) + 4 * K));
     l.rq = take(8 * M);
-    l.dq = take(8 * 7 * M);
+    l.dq = take(align16(mt * 6 * M) + 8 * 2 * M);   // dq (MT), then dq/dT and u terms (FP64)
     l.bytes = off;
     return l;
 }
@@ -665,46 +677,58 @@ static int lu_batched(int32_t n, int64_t batch, MT *A, int32_t *piv, MT *b, int3
 
 // Autotuner for the mechanism mapping (lanes per cell L and cells per CTA):
 // on the first integration of a context created with lanes_per_cell = 0,
-// the first tune_cells cells are copied to scratch and integrated once per
-// candidate (L = 8, 16, 32; the resident-maximising CTA size and half of it),
-// timed with CUDA events on the context's stream; the fastest is kept.
-// The trials are synchronous and leave the caller's state untouched.
+// each candidate (L = 8, 16, 32 at its resident-maximising CTA size)
+// integrates a scratch copy of the first cells -- eight full waves of that
+// mapping, so that the trial measures steady-state throughput rather than
+// the latency of a single wave -- timed with CUDA events on the context's
+// stream; the mapping with the least time per cell is kept.  The trials are
+// synchronous and leave the caller's state untouched.
+static long long resident_cells(sunb_ctx *ctx) { return (long long)ctx->num_sms * ctx->ctas_per_sm * ctx->cells_per_cta; }
+
 static int autotune(sunb_ctx *ctx, const double *dev_y, double t0, double tout)
 {
     const bool mixed = ctx->kind == SUNB_MIXED;
     const double *ysrc = dev_y + (mixed ? ctx->Cc : 0);
-    const size_t bytes = 8 * (size_t)ctx->tune_cells * ctx->N;
     cudaEvent_t e0, e1;
     CU(cudaEventCreate(&e0));
     CU(cudaEventCreate(&e1));
-    float best = 1e30f;
+    double best = 1e300;
     int bestL = ctx->L, bestc = ctx->cells_per_cta;
     const int Ls[3] = {8, 16, 32};
     for (int li = 0; li < 3; ++li) {
-        int rc = configure_mech(ctx, Ls[li]);
-        if (rc != SUNB_SUCCESS) continue;
-        const int cmax = ctx->cells_per_cta;
-        const int step = std::max(1, 32 / Ls[li]);
-        int cands[2] = {cmax, std::max(step, (cmax / 2) / step * step)};
-        for (int ci = 0; ci < 2; ++ci) {
-            if (ci == 1 && cands[1] == cands[0]) { ctx->tune_ms[li][ci] = -1.0f; continue; }
-            if (configure_mech(ctx, Ls[li], cands[ci]) != SUNB_SUCCESS) continue;
-            CU(cudaMemcpyAsync(ctx->d_tune, ysrc, bytes, cudaMemcpyDeviceToDevice, ctx->stream));
-            CU(cudaEventRecord(e0, ctx->stream));
-            int r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, ctx->tune_cells);
-            CU(cudaEventRecord(e1, ctx->stream));
-            CU(cudaEventSynchronize(e1));
-            if (r != SUNB_SUCCESS) return r;
-            float ms = 0.0f;
-            CU(cudaEventElapsedTime(&ms, e0, e1));
-            ctx->tune_ms[li][ci] = ms;
-            if (ms < best) { best = ms; bestL = Ls[li]; bestc = cands[ci]; }
-        }
+        if (configure_mech(ctx, Ls[li]) != SUNB_SUCCESS) { ctx->tune_ms[li][0] = -1.0f; continue; }
+        const long long n = std::min<long long>(ctx->tune_cells, 8 * resident_cells(ctx));
+        CU(cudaMemcpyAsync(ctx->d_tune, ysrc, 8 * (size_t)n * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
+        CU(cudaEventRecord(e0, ctx->stream));
+        int r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, n);
+        CU(cudaEventRecord(e1, ctx->stream));
+        CU(cudaEventSynchronize(e1));
+        if (r != SUNB_SUCCESS) return r;
+        float ms = 0.0f;
+        CU(cudaEventElapsedTime(&ms, e0, e1));
+        ctx->tune_ms[li][0] = ms;
+        ctx->tune_ms[li][1] = (float)n;
+        const double per_cell = ms / (double)n;
+        if (per_cell < best) { best = per_cell; bestL = Ls[li]; bestc = ctx->cells_per_cta; }
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     ctx->tuned = true;
     return configure_mech(ctx, bestL, bestc);
+}
+
+// One warp per cell, up to four cells per CTA within the shared-memory limit.
+static int eval_config(sunb_ctx *ctx, MechArgs &a, int &bytes)
+{
+    int optin = 0;
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    a.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
+    a.cells_per_cta = 4;
+    while (a.cells_per_cta > 1 && ctx->off.bytes + a.cells_per_cta * a.lay.bytes > optin) --a.cells_per_cta;
+    bytes = ctx->off.bytes + a.cells_per_cta * a.lay.bytes;
+    if (bytes > optin) return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for the evaluation kernel");
+    CU(cudaFuncSetAttribute((void *)mech_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    return SUNB_SUCCESS;
 }
 
 extern "C" {
@@ -784,8 +808,12 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
         ctx->autotune = lpc == 0;
         if ((rc = configure_mech(ctx, L)) != SUNB_SUCCESS) return bail(rc);
         if (ctx->autotune) {
-            // enough cells to fill the GPU twice at the densest mapping
-            ctx->tune_cells = std::min<long long>(ctx->C, 2LL * ctx->num_sms * 32);
+            // eight waves of the densest mapping
+            long long most = 0;
+            for (int Lc : {8, 16, 32})
+                if (configure_mech(ctx, Lc) == SUNB_SUCCESS) most = std::max(most, resident_cells(ctx));
+            if ((rc = configure_mech(ctx, L)) != SUNB_SUCCESS) return bail(rc);
+            ctx->tune_cells = std::min<long long>(ctx->C, 8 * most);
             if (ctx->tune_cells >= 1 &&
                 cudaMalloc(&ctx->d_tune, 8 * (size_t)ctx->tune_cells * ctx->N) != cudaSuccess) {
                 fail(ctx, SUNB_MEM_FAIL, "cudaMalloc autotuning scratch");
@@ -914,12 +942,12 @@ int sunb_rhs(sunb_ctx *ctx, const double *dev_y, double *dev_f, int64_t n_cells)
     if (n_cells == 0) return SUNB_SUCCESS;
     if (ctx->kind == SUNB_MECHANISM) {
         MechArgs a = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
-        a.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
-        a.cells_per_cta = 4;
-        const int bytes = ctx->off.bytes + 4 * a.lay.bytes;
-        CU(cudaFuncSetAttribute((void *)mech_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        const int grid = (int)std::min<long long>((n_cells + 3) / 4, 8LL * ctx->num_sms);
-        mech_eval_kernel<<<grid, 128, bytes, ctx->stream>>>(a, dev_y, dev_f, n_cells, 0);
+        int bytes = 0;
+        const int rc = eval_config(ctx, a, bytes);
+        if (rc != SUNB_SUCCESS) return rc;
+        const int grid = (int)std::min<long long>((n_cells + a.cells_per_cta - 1) / a.cells_per_cta,
+                                                  8LL * ctx->num_sms);
+        mech_eval_kernel<<<grid, 32 * a.cells_per_cta, bytes, ctx->stream>>>(a, dev_y, dev_f, n_cells, 0);
     } else {
         ThreadArgs a = thread_args(ctx, nullptr, 0.0, 0.0, nullptr);
         const int grid = (int)std::min<long long>((n_cells + 127) / 128, 8LL * ctx->num_sms);
@@ -940,12 +968,12 @@ int sunb_jac(sunb_ctx *ctx, const double *dev_y, double *dev_J, int64_t n_cells)
     if (n_cells == 0) return SUNB_SUCCESS;
     if (ctx->kind == SUNB_MECHANISM) {
         MechArgs a = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
-        a.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
-        a.cells_per_cta = 4;
-        const int bytes = ctx->off.bytes + 4 * a.lay.bytes;
-        CU(cudaFuncSetAttribute((void *)mech_eval_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
-        const int grid = (int)std::min<long long>((n_cells + 3) / 4, 8LL * ctx->num_sms);
-        mech_eval_kernel<<<grid, 128, bytes, ctx->stream>>>(a, dev_y, dev_J, n_cells, 1);
+        int bytes = 0;
+        const int rc = eval_config(ctx, a, bytes);
+        if (rc != SUNB_SUCCESS) return rc;
+        const int grid = (int)std::min<long long>((n_cells + a.cells_per_cta - 1) / a.cells_per_cta,
+                                                  8LL * ctx->num_sms);
+        mech_eval_kernel<<<grid, 32 * a.cells_per_cta, bytes, ctx->stream>>>(a, dev_y, dev_J, n_cells, 1);
     } else {
         ThreadArgs a = thread_args(ctx, nullptr, 0.0, 0.0, nullptr);
         const int grid = (int)std::min<long long>((n_cells + 127) / 128, 8LL * ctx->num_sms);
