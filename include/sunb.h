@@ -187,6 +187,30 @@ int64_t sunb_get_launch_count(const sunb_ctx *ctx);
 
 int sunb_destroy(sunb_ctx *ctx);
 
+/* Integrate n_cells Robertson cells (the kind SUNB_ROBERTSON integrates)
+ * from t0 to tout without allocating anything: no context, no cudaMalloc,
+ * cudaFree or other allocating call.  It is meant for callers that own all
+ * device memory themselves and may not allocate once their time loop runs.
+ * The paper has no counterpart; the method is the one of sunb_integrate.
+ *  - dev_k [n_cells,3] (k1, k2, k3) and dev_y [n_cells,3] (advanced in
+ *    place) are caller-owned device arrays; host_atol points to 3 host
+ *    doubles; dev_status (nullable, int32 [n_cells]) receives the per-cell
+ *    statuses; max_steps <= 0 means 100000; stream is a cudaStream_t.
+ *  - The work queue and the per-cell counters live in one static device
+ *    array of 2 MiB + 256 bytes that every GPU loading the library keeps
+ *    until the process exits; it limits n_cells to 65536 (larger batches
+ *    return SUNB_ILL_INPUT before anything is enqueued).
+ *  - The first call on a device looks up that array's device address (with
+ *    the device current) and caches it; make that first call before any
+ *    stream capture.  The counter is cleared on every call.
+ *  - All calls share the array: calls whose work overlaps on the GPU (on
+ *    different streams, or from several host threads) race; serialise them.
+ *  - Asynchronous on stream; returns launch errors only; errors are
+ *    described by sunb_last_error(NULL). */
+int sunb_integrate_robertson_noalloc(const double *dev_k, double *dev_y, int64_t n_cells,
+                                     double t0, double tout, double rtol, const double *host_atol,
+                                     int32_t max_steps, int32_t *dev_status, void *stream);
+
 /* Description of the last failure of ctx (or of a failed create when ctx is
  * NULL); never NULL. */
 const char *sunb_last_error(const sunb_ctx *ctx);

@@ -83,6 +83,9 @@ SIGNATURES = {
     "sunb_get_launch_count": (ctypes.c_int64, [_vp]),
     "sunb_get_mapping": (ctypes.c_int, [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
     "sunb_destroy": (ctypes.c_int, [_vp]),
+    "sunb_integrate_robertson_noalloc": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, ctypes.c_double,
+                                                         ctypes.c_double, ctypes.c_double, _dp,
+                                                         ctypes.c_int32, _vp, _vp]),
     "sunb_last_error": (ctypes.c_char_p, [_vp]),
     "sunb_version": (ctypes.c_char_p, []),
 }
@@ -260,6 +263,19 @@ def lu_solve_batched(A, b, stream=None):
     fn = lib().sunb_lu_solve_batched if A.dtype == torch.float64 else lib().sunb_lu_solve_batched_f32
     _check(fn(n, B, _ptr(A), _ptr(piv), _ptr(b), _ptr(info), _stream_handle(stream)))
     return piv, info
+
+
+def integrate_robertson_noalloc(k, y, t0, tout, rtol, atol, status=None, max_steps=0,
+                                stream=None):
+    """Robertson cells through the allocation-free entry point (for callers
+    that may not allocate device memory): k, y float64 CUDA tensors [C, 3],
+    y advanced in place; at most 65536 cells per call; calls that overlap on
+    the GPU share one static scratch array and must not run concurrently."""
+    a = _cont(np.broadcast_to(np.asarray(atol, dtype=np.float64), (3,)), np.float64)
+    rc = lib().sunb_integrate_robertson_noalloc(_ptr(k), _ptr(y), y.shape[0], t0, tout, rtol,
+                                                a.ctypes.data_as(_dp), max_steps, _ptr(status),
+                                                _stream_handle(stream))
+    _check(rc, None)
 
 
 def from_workload(w, precision=FP64, lanes_per_cell=0, schedule=SCHED_QUEUE, max_steps=100000,

@@ -30,11 +30,12 @@ def up_to_date():
 
 
 def build(force=False, verbose=False):
-    """Compile csrc/sunb_api.cu (which includes the kernel headers)."""
+    """Compile the translation units of csrc/ (sunb_api.cu includes the
+    kernel headers; sunb_noalloc.cu holds the allocation-free entry point)."""
     if not force and up_to_date():
         return LIB
-    cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + \
-        ["-o", LIB + ".tmp", os.path.join(CSRC, "sunb_api.cu")]
+    units = [os.path.join(CSRC, f) for f in ("sunb_api.cu", "sunb_noalloc.cu")]
+    cmd = [NVCC] + FLAGS + (["-Xptxas", "-v"] if verbose else []) + ["-o", LIB + ".tmp"] + units
     subprocess.check_call(cmd)
     os.replace(LIB + ".tmp", LIB)
     return LIB

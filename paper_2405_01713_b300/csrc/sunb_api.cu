@@ -366,6 +366,9 @@ struct sunb_ctx {
 
 static std::string g_create_error = "no error";
 
+// Message for sunb_last_error(NULL) from entry points that have no context.
+void sunb_internal_set_error(const std::string &msg) { g_create_error = msg; }
+
 static int fail(sunb_ctx *ctx, int code, const std::string &msg)
 {
     if (ctx) ctx->err = msg; else g_create_error = msg;
