@@ -95,7 +95,8 @@ typedef struct {
     int32_t precision;        /* sunb_precision: FP32 Newton matrix/LU if MIXED32 */
     int32_t lanes_per_cell;   /* mechanism cells: 8, 16, 32, or 0 = autotune  */
     int32_t schedule;         /* sunb_schedule                                */
-    int32_t record_adjoint;   /* reserved, must be 0                          */
+    int32_t record_adjoint;   /* 0, or the tape capacity (accepted steps per
+                                 cell) for sunb_adjoint; SUNB_MECHANISM only  */
     const sunb_mechanism *mech;        /* SUNB_MECHANISM, SUNB_MIXED */
     const sunb_cooling_table *table;   /* SUNB_COSMOLOGY, SUNB_MIXED */
 } sunb_problem;
@@ -168,6 +169,32 @@ int sunb_lu_solve_batched(int32_t n, int64_t batch, double *dev_A, int32_t *dev_
  * mixed form). */
 int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *dev_piv,
                               float *dev_b, int32_t *dev_info, void *stream);
+
+/* Discrete adjoint (spec differentiation extension; the paper only
+ * names the sensitivity-capable packages CVODES/IDAS, Sec. 2).  With
+ * record_adjoint = cap > 0 at create, sunb_integrate records per cell and
+ * accepted step the state, the Nordsieck column map applied since the
+ * previous step, the update vector, gamma and 1/l_1 (at most cap steps; a
+ * cell that needs more is marked and gets NaN results below).  The
+ * differentiated map freezes step sizes, orders and column maps and treats
+ * every corrector as solved exactly.
+ * sunb_adjoint_replay recomputes the step history from the tapes with each
+ * corrector solved by full Newton to rounding level (fresh analytic
+ * Jacobian per iteration) and writes the final states of that map to
+ * dev_y_final (nullable, [C, N]): evaluate the loss there. */
+int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final);
+
+/* Gradient of a loss L(y_final) with dev_dLdy = dL/dy_final ([C, N], device)
+ * with respect to (ln A_j, Ea_j): dev_grad [M, 2] = sum over cells (fixed
+ * summation order, so repeated calls give the same bytes); dev_grad_cells
+ * (nullable, [C, M, 2]) receives the per-cell gradients.  Replays first if
+ * sunb_adjoint_replay was not called after the last sunb_integrate.
+ * Returns SUNB_NO_RECORD for a context without tapes. */
+int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double *dev_grad_cells);
+
+/* Replace the Arrhenius parameters ln A_j and Ea_j (host arrays [M]) of a
+ * mechanism context; synchronises the context's stream. */
+int sunb_set_arrhenius(sunb_ctx *ctx, const double *host_lnA, const double *host_Ea);
 
 /* Lanes per mechanism cell chosen by the context (autotuned when asked). */
 int sunb_get_lanes_per_cell(const sunb_ctx *ctx);

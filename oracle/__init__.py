@@ -77,6 +77,22 @@ def lib():
         L.orc_bdf_fixed.argtypes = [PP, ctypes.c_long, ctypes.c_int, ctypes.c_double, ctypes.c_int,
                                     _dp, _dp, _dp, _dp, _dp, _dp]
         L.orc_bdf_fixed.restype = ctypes.c_int
+        L.orc_tape_new.argtypes = [ctypes.c_int, ctypes.c_int]
+        L.orc_tape_new.restype = ctypes.c_void_p
+        L.orc_tape_free.argtypes = [ctypes.c_void_p]
+        L.orc_tape_count.argtypes = [ctypes.c_void_p]
+        L.orc_tape_count.restype = ctypes.c_int
+        L.orc_forward_tape.argtypes = [PP, ctypes.c_long, _dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.POINTER(Options), _ip, ctypes.c_void_p]
+        L.orc_forward_tape.restype = ctypes.c_int
+        L.orc_adjoint_tape.argtypes = [PP, ctypes.c_long, ctypes.c_void_p, _dp, _dp]
+        L.orc_adjoint_tape.restype = ctypes.c_int
+        L.orc_replay_tape.argtypes = [PP, ctypes.c_long, ctypes.c_void_p, _dp]
+        L.orc_replay_tape.restype = ctypes.c_int
+        L.orc_rhs_dlnA.argtypes = [PP, ctypes.c_long, _dp, _dp]
+        L.orc_adjoint_sqerr.argtypes = [PP, ctypes.c_long, _dp, _dp, ctypes.c_double, ctypes.c_double,
+                                        ctypes.POINTER(Options), ctypes.c_int, _dp, _dp, ctypes.c_int]
+        L.orc_adjoint_sqerr.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -234,3 +250,75 @@ def bdf_fixed(pb, q, h, nsteps, zinit, hist, cell=0):
 
 def num_threads():
     return lib().orc_num_threads()
+
+
+# ------------------------------------------------------------- discrete adjoint
+class Tape:
+    """The frozen forward map of one cell (accepted steps with their column
+    maps, update vectors, gamma, 1/l_1 and states), for the adjoint."""
+
+    def __init__(self, n, cap=8192):
+        self.n = n
+        self.ptr = lib().orc_tape_new(n, cap)
+
+    @property
+    def steps(self):
+        return lib().orc_tape_count(self.ptr)
+
+    def __del__(self):
+        if getattr(self, "ptr", None):
+            lib().orc_tape_free(self.ptr)
+            self.ptr = None
+
+
+def forward_tape(pb, y0, t0, tout, rtol, atol, cell=0, max_steps=100000, cap=8192, max_order=5):
+    """Integrate one cell and record its tape: returns (y, stats, tape)."""
+    y = _f64(y0).copy().reshape(pb.n)
+    atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
+    o = Options(rtol, _d(atol), max_steps, max_order, 0)
+    st = np.zeros(8, dtype=np.int32)
+    tp = Tape(pb.n, cap)
+    lib().orc_forward_tape(pb.ref, cell, _d(y), t0, tout, ctypes.byref(o), _i(st), tp.ptr)
+    if tp.steps < 0:
+        raise RuntimeError("tape overflow")
+    return y, st, tp
+
+
+def adjoint_tape(pb, tape, dLdy, cell=0):
+    """Gradient [M, 2] of the loss with d loss / d y_final = dLdy with respect
+    to (ln A_j, Ea_j), through the frozen map of the tape."""
+    g = np.zeros((pb.s.M, 2))
+    rc = lib().orc_adjoint_tape(pb.ref, cell, tape.ptr, _d(_f64(dLdy)), _d(g))
+    if rc:
+        raise RuntimeError(f"adjoint failed ({rc})")
+    return g
+
+
+def replay_tape(pb, tape, cell=0):
+    """Final state of the tape's frozen map with pb's current parameters."""
+    y = np.empty(pb.n)
+    rc = lib().orc_replay_tape(pb.ref, cell, tape.ptr, _d(y))
+    if rc:
+        raise RuntimeError(f"replay failed ({rc})")
+    return y
+
+
+def rhs_dlnA(pb, y, cell=0):
+    F = np.empty((pb.s.M, pb.n))
+    lib().orc_rhs_dlnA(pb.ref, cell, _d(_f64(y)), _d(F))
+    return F
+
+
+def adjoint_sqerr(pb, y0, target, t0, tout, rtol, atol, cap=8192, nthreads=0, max_steps=100000):
+    """Per cell: final state of the exact-corrector replay and the gradient
+    [C, M, 2] of sum_k (Y_k - target_k)^2 with respect to (ln A, Ea)."""
+    y0 = _f64(y0).reshape(-1, pb.n)
+    C = y0.shape[0]
+    target = _f64(target).reshape(C, -1)
+    atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
+    o = Options(rtol, _d(atol), max_steps, 5, 0)
+    yrep = np.zeros((C, pb.n))
+    grad = np.zeros((C, pb.s.M, 2))
+    nbad = lib().orc_adjoint_sqerr(pb.ref, C, _d(y0), _d(target), t0, tout, ctypes.byref(o), cap,
+                                   _d(yrep), _d(grad), nthreads)
+    return yrep, grad, nbad

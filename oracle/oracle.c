@@ -288,17 +288,71 @@ static double initial_step(const orc_problem *pb, long cell, double t0, double t
     return fmin(h, span);
 }
 
-/* Optional per-step record for the discrete adjoint. */
+/* ---- discrete-adjoint tape --------------------------------------------
+ * The forward map of one cell, frozen: the initial array [y0, h0 f(y0)],
+ * then per accepted step n
+ *   Z_pre  = P_n Z_{n-1}      (column map: rescales and order decreases
+ *                              applied since the previous accepted step)
+ *   Z_pred = Z_pre . Pascal   (prediction)
+ *   y_n    : y - gamma f(y) - (z0_pred - z1_pred / l_1) = 0
+ *   Z_n    = Z_pred + c_n (y_n - z0_pred)   (c = l, plus the terms of an
+ *                              order increase decided after the step)
+ * Record layout (doubles): y_n [n], P [6][6] (row = output column,
+ * column = input column), c [6], gamma, 1/l_1, q, q_out (highest column of
+ * Z_n).  Step sizes and orders are frozen; each corrector counts as solved
+ * exactly (implicit function theorem with the exact Jacobian). */
+#define TAPE_R(n) ((n) + 46)
 typedef struct {
-    int cap, count;
-    double *t, *h, *y;     /* accepted step end time, size, state [count, n] */
-    int *q;
-} step_log;
+    int n, cap, count, overflow;
+    double h0;
+    double *y0;     /* [n] */
+    double *rec;    /* [cap][TAPE_R(n)] */
+    double P[36];   /* map accumulated since the last accepted step */
+} orc_tape;
+
+static void tape_reset_map(orc_tape *tp)
+{
+    for (int i = 0; i < 36; ++i) tp->P[i] = (i % 7 == 0) ? 1.0 : 0.0;
+}
+
+/* the column operations of the integrator, mirrored on the tape's map */
+static void tape_rescale(orc_tape *tp, int q, double eta)
+{
+    if (!tp) return;
+    double f = 1.0;
+    for (int o = 1; o <= q; ++o) {
+        f *= eta;
+        for (int i = 0; i < 6; ++i) tp->P[o * 6 + i] *= f;
+    }
+}
+
+static void tape_decrease(orc_tape *tp, int q, const double *nodes)
+{
+    if (!tp) return;
+    orc_order_decrease(q, 6, tp->P, nodes);   /* rows of P act as columns */
+}
+
+static void tape_record(orc_tape *tp, const double *y, const double *c, double gamma,
+                        double il1, int q, int q_out)
+{
+    if (!tp) return;
+    if (tp->count >= tp->cap) { tp->overflow = 1; return; }
+    const int n = tp->n;
+    double *r = tp->rec + (size_t)tp->count * TAPE_R(n);
+    memcpy(r, y, sizeof(double) * n);
+    memcpy(r + n, tp->P, sizeof(double) * 36);
+    memcpy(r + n + 36, c, sizeof(double) * 6);
+    r[n + 42] = gamma;
+    r[n + 43] = il1;
+    r[n + 44] = q;
+    r[n + 45] = q_out;
+    tp->count++;
+}
 
 /* ---- one cell, one call: t0 -> tout ------------------------------------- */
 static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                     double tout, const orc_options *op, orc_stats *st,
-                    double *hlast)
+                    double *hlast, orc_tape *tp)
 {
     const int n = pb->n;
     const int qmax = op->max_order < 1 ? 1 : (op->max_order > QMAX ? QMAX : op->max_order);
@@ -325,6 +379,11 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
     set_weights(n, y, op->rtol, op->atol, w);
     h = initial_step(pb, cell, t0, tout, y, f, w, ycur, tmp, &s.nfe);
     for (int k = 0; k < n; ++k) z[n + k] = h * f[k];
+    if (tp) {
+        memcpy(tp->y0, y, sizeof(double) * n);
+        tp->h0 = h;
+        tape_reset_map(tp);
+    }
 
     while (t < tout) {
         if (s.nst >= op->max_steps) { s.status = ORC_TOO_MUCH_WORK; break; }
@@ -333,6 +392,7 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
         if (t + h >= tout || tout - (t + h) <= 4.0 * DBL_EPSILON * fabs(tout)) {
             double hn = tout - t;
             rescale(q, n, z, hn / h);
+            tape_rescale(tp, q, hn / h);
             h = hn;
             last = 1;
         }
@@ -388,7 +448,7 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                 memcpy(z, zsave, sizeof(double) * (q + 1) * n);
                 s.ncf++; ncf++;
                 if (ncf >= 10) { s.status = ORC_CONV_FAILURE; break; }
-                h *= 0.25; rescale(q, n, z, 0.25);
+                h *= 0.25; rescale(q, n, z, 0.25); tape_rescale(tp, q, 0.25);
                 force_setup = 1; etamax = 1.0; last = 0;
                 if (t + h == t) { s.status = ORC_H_TOO_SMALL; break; }
                 continue;
@@ -414,9 +474,10 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                     double nodes[QMAX], sacc = 0.0;
                     for (int i = 0; i < q - 1; ++i) { sacc += hist[i]; nodes[i] = sacc / h; }
                     orc_order_decrease(q, n, z, nodes);
+                    tape_decrease(tp, q, nodes);
                     q = newq; qwait = q + 1;
                 }
-                h *= eta; rescale(q, n, z, eta);
+                h *= eta; rescale(q, n, z, eta); tape_rescale(tp, q, eta);
             } else {
                 /* from the third failure: order 1 and eta = 0.1; the order
                  * is lowered through the interpolating polynomials, which
@@ -425,9 +486,9 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                 if (q > 1) {
                     double nodes[QMAX], sacc = 0.0;
                     for (int i = 0; i < q - 1; ++i) { sacc += hist[i]; nodes[i] = sacc / h; }
-                    for (; q > 1; --q) orc_order_decrease(q, n, z, nodes);
+                    for (; q > 1; --q) { orc_order_decrease(q, n, z, nodes); tape_decrease(tp, q, nodes); }
                 }
-                h *= eta; rescale(q, n, z, eta);
+                h *= eta; rescale(q, n, z, eta); tape_rescale(tp, q, eta);
                 qwait = 2; have_ksave = 0;
             }
             etamax = 1.0; last = 0;
@@ -442,7 +503,12 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
             for (int i = 0; i < n; ++i) z[j * n + i] += l[j] * acor[i];
         for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
         hist[0] = h;
-        if (last) break;
+        double cvec[6] = {0, 0, 0, 0, 0, 0};
+        for (int j = 0; j <= q; ++j) cvec[j] = l[j];
+        if (last) {
+            tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, q);
+            break;
+        }
 
         /* step size and order for the next step */
         qwait--;
@@ -469,8 +535,12 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
         }
         if (eta < 1.5) { eta = 1.0; newq = q; }
         else eta = fmin(eta, etamax);
+        if (newq == q + 1)
+            for (int j = 1; j <= q + 1; ++j) cvec[j] += l[j - 1] / xi[q];
+        tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, newq == q + 1 ? q + 1 : q);
+        if (tp) tape_reset_map(tp);
         if (newq == q + 1) orc_order_increase(q, n, z, acor, l, xi[q]);
-        else if (newq == q - 1) orc_order_decrease(q, n, z, xi);
+        else if (newq == q - 1) { orc_order_decrease(q, n, z, xi); tape_decrease(tp, q, xi); }
         if (newq != q || qwait == 0) { q = newq; qwait = q + 1; have_ksave = 0; }
         if (qwait == 1 && q < qmax) {
             for (int i = 0; i < n; ++i) ksave[i] = kfac * acor[i];
@@ -478,6 +548,7 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
         }
         h *= eta;
         rescale(q, n, z, eta);
+        tape_rescale(tp, q, eta);
         etamax = 10.0;
     }
     memcpy(y, z, sizeof(double) * n);
@@ -510,7 +581,7 @@ EXPORT int orc_integrate(const orc_problem *pb, long ncells, double *y, double t
 #pragma omp parallel for schedule(dynamic, 4) reduction(min : worst)
     for (long c = 0; c < ncells; ++c) {
         int r = bdf_cell(pb, c, y + (size_t)c * pb->n, t0, tout, op,
-                         stats ? stats + c : NULL, hlast ? hlast + c : NULL);
+                         stats ? stats + c : NULL, hlast ? hlast + c : NULL, NULL);
         if (r < worst) worst = r;
     }
     return worst;
@@ -581,4 +652,225 @@ EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int 
     memcpy(y_out, z, sizeof(double) * n);
     if (z_out) memcpy(z_out, z, sizeof(double) * (q + 1) * n);
     return 0;
+}
+
+/* ---- discrete adjoint (the spec differentiation extension) --------
+ * Gradient of a loss on the final state with respect to the Arrhenius
+ * parameters (ln A_j, Ea_j) of the frozen forward map recorded on the tape
+ * (see orc_tape).  Reverse sweep: lam is the adjoint of the Nordsieck array;
+ * at each step mu = (I - gamma J(y_n))^{-T} lam_Delta, the parameter term
+ * gamma (df/dtheta)^T mu is accumulated, and lam is carried back through the
+ * corrector's a_n, the prediction and the column map.  J is the
+ * complex-step Jacobian at y_n; df/d ln A_j is the right-hand side with the
+ * rates of progress of reaction j alone (f is linear in them and
+ * dq_j/d ln A_j = q_j); df/dEa_j = -df/d ln A_j / (Rc T). */
+EXPORT orc_tape *orc_tape_new(int n, int cap)
+{
+    orc_tape *tp = calloc(1, sizeof(orc_tape));
+    tp->n = n;
+    tp->cap = cap;
+    tp->y0 = calloc((size_t)n, sizeof(double));
+    tp->rec = calloc((size_t)cap * TAPE_R(n), sizeof(double));
+    tape_reset_map(tp);
+    return tp;
+}
+
+EXPORT void orc_tape_free(orc_tape *tp)
+{
+    if (!tp) return;
+    free(tp->y0);
+    free(tp->rec);
+    free(tp);
+}
+
+EXPORT int orc_tape_count(const orc_tape *tp) { return tp->overflow ? -1 : tp->count; }
+
+EXPORT int orc_forward_tape(const orc_problem *pb, long cell, double *y, double t0, double tout,
+                            const orc_options *op, orc_stats *st, orc_tape *tp)
+{
+    tp->count = 0;
+    tp->overflow = 0;
+    return bdf_cell(pb, cell, y, t0, tout, op, st, NULL, tp);
+}
+
+/* F[j*n + i] = d f_i / d ln A_j at y (mechanism problems) */
+EXPORT void orc_rhs_dlnA(const orc_problem *pb, long cell, const double *y, double *F)
+{
+    const double *prm = pb->params + (size_t)cell * pb->nparams;
+    for (int j = 0; j < pb->M; ++j) rhs_mechanism_r(pb, prm, y, F + (size_t)j * pb->n, j);
+}
+
+static void theta_term(const orc_problem *pb, long cell, const double *y, const double *v,
+                       double scale, double *grad, double *Fj)
+{
+    const int n = pb->n, M = pb->M;
+    const double *prm = pb->params + (size_t)cell * pb->nparams;
+    const double T = y[pb->K];
+    for (int j = 0; j < M; ++j) {
+        rhs_mechanism_r(pb, prm, y, Fj, j);
+        double d = 0.0;
+        for (int i = 0; i < n; ++i) d += Fj[i] * v[i];
+        grad[2 * j] += scale * d;
+        grad[2 * j + 1] += -scale * d / (ORC_RC * T);
+    }
+}
+
+static int replay(const orc_problem *pb, long cell, const orc_tape *tp, double *yout, double *ys);
+
+/* The loss is taken at the replayed final state (the map with exact
+ * correctors): the forward run's states solve their correctors only to the
+ * Newton tolerance, so the step history is first recomputed from the tape
+ * (y0, h0 and the frozen coefficients), then swept backwards. */
+EXPORT int orc_adjoint_tape(const orc_problem *pb, long cell, const orc_tape *tp,
+                            const double *dLdy, double *grad)
+{
+    const int n = pb->n, M = pb->M, R = TAPE_R(n);
+    if (tp->overflow || pb->kind != ORC_MECHANISM) return -1;
+    double *ys = malloc(sizeof(double) * (size_t)n * (tp->count > 0 ? tp->count : 1));
+    double *yfin = malloc(sizeof(double) * n);
+    if (replay(pb, cell, tp, yfin, ys)) { free(ys); free(yfin); return -2; }
+    free(yfin);
+    double *lam = calloc(6 * (size_t)n, sizeof(double)), *nl = calloc(6 * (size_t)n, sizeof(double));
+    double *ld = malloc(sizeof(double) * n), *J = malloc(sizeof(double) * n * n);
+    double *Mt = malloc(sizeof(double) * n * n), *f = malloc(sizeof(double) * n);
+    double *w = malloc(sizeof(double) * n), *Fj = malloc(sizeof(double) * n);
+    int32_t *piv = malloc(sizeof(int32_t) * n);
+    int rc = 0;
+    for (int j = 0; j < 2 * M; ++j) grad[j] = 0.0;
+    for (int i = 0; i < n; ++i) { lam[i] = dLdy[i]; w[i] = 1.0; }
+    for (int r = tp->count - 1; r >= 0; --r) {
+        const double *rec = tp->rec + (size_t)r * R;
+        const double *y = ys + (size_t)r * n, *P = rec + n, *c = rec + n + 36;
+        const double gamma = rec[n + 42], il1 = rec[n + 43];
+        const int q = (int)rec[n + 44], qo = (int)rec[n + 45];
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int j = 0; j <= qo; ++j) s += c[j] * lam[j * n + i];
+            ld[i] = s;
+        }
+        for (int j = q + 1; j < 6; ++j)
+            for (int i = 0; i < n; ++i) lam[j * n + i] = 0.0;
+        for (int i = 0; i < n; ++i) lam[i] -= ld[i];
+        /* mu = (I - gamma J)^{-T} lam_Delta */
+        orc_jac(pb, cell, y, f, w, 0, J);
+        for (int a = 0; a < n; ++a)
+            for (int b = 0; b < n; ++b) Mt[a * n + b] = (a == b ? 1.0 : 0.0) - gamma * J[b * n + a];
+        if (orc_lu_factor(n, Mt, piv)) { rc = -2; break; }
+        orc_lu_solve(n, Mt, piv, ld);      /* ld now holds mu */
+        theta_term(pb, cell, y, ld, gamma, grad, Fj);
+        for (int i = 0; i < n; ++i) { lam[i] += ld[i]; lam[n + i] -= il1 * ld[i]; }
+        /* transpose of the prediction */
+        for (int k = q - 1; k >= 0; --k)
+            for (int j = k + 1; j <= q; ++j)
+                for (int i = 0; i < n; ++i) lam[j * n + i] += lam[(j - 1) * n + i];
+        /* transpose of the column map */
+        for (int a = 0; a < 6; ++a)
+            for (int i = 0; i < n; ++i) {
+                double s = 0.0;
+                for (int o = 0; o < 6; ++o) s += P[o * 6 + a] * lam[o * n + i];
+                nl[a * n + i] = s;
+            }
+        memcpy(lam, nl, sizeof(double) * 6 * n);
+    }
+    if (rc == 0) theta_term(pb, cell, tp->y0, lam + n, tp->h0, grad, Fj);  /* z1 = h0 f(y0) */
+    free(ys);
+    free(lam); free(nl); free(ld); free(J); free(Mt); free(f); free(w); free(Fj); free(piv);
+    return rc;
+}
+
+/* Re-run the frozen map of the tape with the problem's current parameters,
+ * each corrector solved by full Newton (fresh complex-step Jacobian every
+ * iteration) to rounding level.  ys (nullable) receives the exact y_n. */
+static int replay(const orc_problem *pb, long cell, const orc_tape *tp, double *yout, double *ys)
+{
+    const int n = pb->n, R = TAPE_R(n);
+    double *Z = calloc(6 * (size_t)n, sizeof(double)), *Zp = calloc(6 * (size_t)n, sizeof(double));
+    double *y = malloc(sizeof(double) * n), *f = malloc(sizeof(double) * n);
+    double *J = malloc(sizeof(double) * n * n), *w = malloc(sizeof(double) * n);
+    double *g = malloc(sizeof(double) * n);
+    int32_t *piv = malloc(sizeof(int32_t) * n);
+    int rc = 0;
+    for (int i = 0; i < n; ++i) w[i] = 1.0;
+    memcpy(Z, tp->y0, sizeof(double) * n);
+    rhs_r(pb, cell, tp->y0, f);
+    for (int i = 0; i < n; ++i) Z[n + i] = tp->h0 * f[i];
+    for (int r = 0; r < tp->count && rc == 0; ++r) {
+        const double *rec = tp->rec + (size_t)r * R;
+        const double *P = rec + n, *c = rec + n + 36;
+        const double gamma = rec[n + 42], il1 = rec[n + 43];
+        const int q = (int)rec[n + 44], qo = (int)rec[n + 45];
+        for (int o = 0; o < 6; ++o)
+            for (int i = 0; i < n; ++i) {
+                double sacc = 0.0;
+                for (int a = 0; a < 6; ++a) sacc += P[o * 6 + a] * Z[a * n + i];
+                Zp[o * n + i] = sacc;
+            }
+        for (int k = 0; k < q; ++k)
+            for (int j = q; j > k; --j)
+                for (int i = 0; i < n; ++i) Zp[(j - 1) * n + i] += Zp[j * n + i];
+        memcpy(y, rec, sizeof(double) * n);        /* the recorded state is the first guess */
+        for (int it = 0; it < 60; ++it) {
+            rhs_r(pb, cell, y, f);
+            for (int i = 0; i < n; ++i) g[i] = -(y[i] - gamma * f[i] - (Zp[i] - il1 * Zp[n + i]));
+            orc_jac(pb, cell, y, f, w, 0, J);
+            for (int i = 0; i < n * n; ++i) J[i] = -gamma * J[i];
+            for (int i = 0; i < n; ++i) J[i * n + i] += 1.0;
+            if (orc_lu_factor(n, J, piv)) { rc = -2; break; }
+            orc_lu_solve(n, J, piv, g);
+            int done = 1;            /* converged in every component */
+            for (int i = 0; i < n; ++i) {
+                y[i] += g[i];
+                if (fabs(g[i]) > 1e-13 * fabs(y[i]) + 1e-30) done = 0;
+            }
+            if (done) break;
+        }
+        if (ys) memcpy(ys + (size_t)r * n, y, sizeof(double) * n);
+        for (int j = 0; j < 6; ++j)
+            for (int i = 0; i < n; ++i) {
+                const double d = y[i] - Zp[i];
+                Z[j * n + i] = (j <= qo) ? ((j <= q ? Zp[j * n + i] : 0.0) + c[j] * d) : 0.0;
+            }
+    }
+    memcpy(yout, Z, sizeof(double) * n);
+    free(Z); free(Zp); free(y); free(f); free(J); free(w); free(g); free(piv);
+    return rc;
+}
+
+EXPORT int orc_replay_tape(const orc_problem *pb, long cell, const orc_tape *tp, double *yout)
+{
+    return replay(pb, cell, tp, yout, NULL);
+}
+
+/* Squared-error loss sum_k (Y_k - target_k)^2 at the replayed final state,
+ * per cell in parallel: integrate with a tape, replay, adjoint.  yrep
+ * [C, n], grad [C, M, 2]; returns the number of cells that failed. */
+EXPORT int orc_adjoint_sqerr(const orc_problem *pb, long ncells, const double *y0,
+                             const double *target, double t0, double tout,
+                             const orc_options *op, int cap, double *yrep, double *grad,
+                             int nthreads)
+{
+    int nbad = 0;
+#ifdef _OPENMP
+    if (nthreads > 0) omp_set_num_threads(nthreads);
+#else
+    (void)nthreads;
+#endif
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : nbad)
+    for (long c = 0; c < ncells; ++c) {
+        const int n = pb->n, K = pb->K;
+        orc_tape *tp = orc_tape_new(n, cap);
+        double *y = malloc(sizeof(double) * n), *dL = malloc(sizeof(double) * n);
+        memcpy(y, y0 + (size_t)c * n, sizeof(double) * n);
+        int bad = bdf_cell(pb, c, y, t0, tout, op, NULL, NULL, tp) != 0 || tp->overflow;
+        if (!bad) bad = orc_replay_tape(pb, c, tp, yrep + (size_t)c * n) != 0;
+        if (!bad) {
+            for (int i = 0; i < n; ++i)
+                dL[i] = i < K ? 2.0 * (yrep[(size_t)c * n + i] - target[(size_t)c * K + i]) : 0.0;
+            bad = orc_adjoint_tape(pb, c, tp, dL, grad + (size_t)c * 2 * pb->M) != 0;
+        }
+        nbad += bad;
+        free(y); free(dL);
+        orc_tape_free(tp);
+    }
+    return nbad;
 }

@@ -36,9 +36,11 @@ static void FN(rhs_robertson)(const double *k, const REAL *y, REAL *f)
  *   dY_k/dt  = wdot_k W_k / rho
  *   dT/dt    = -sum_k H_k wdot_k / (rho cp),  H_k = Ru T (h/RT)_k,
  *              cp = Ru sum_k Y_k (cp/R)_k / W_k
- * with single-range NASA-7 polynomials for cp/R, h/RT and s/R. */
+ * with single-range NASA-7 polynomials for cp/R, h/RT and s/R.  With
+ * only >= 0, wdot keeps reaction `only` alone (f is linear in the rates of
+ * progress, so this is d f / d ln A_only). */
 static void FN(rhs_mechanism)(const orc_problem *pb, const double *prm,
-                              const REAL *y, REAL *f)
+                              const REAL *y, REAL *f, int only)
 {
     const int K = pb->K, M = pb->M;
     const double P = prm[0];
@@ -63,6 +65,7 @@ static void FN(rhs_mechanism)(const orc_problem *pb, const double *prm,
     }
     REAL patm_RT = ORC_PATM / (ORC_RU * T);
     for (int j = 0; j < M; ++j) {
+        if (only >= 0 && j != only) continue;   /* one reaction's share of wdot */
         const int *r = pb->react + 3 * j, *p = pb->prod + 3 * j;
         REAL kf = EXPF(pb->lnA[j] + pb->beta[j] * lnT - pb->Ea[j] / (ORC_RC * T));
         REAL dG = 0.0;
@@ -140,7 +143,7 @@ static void FN(rhs)(const orc_problem *pb, long cell, const REAL *y, REAL *f)
     const double *prm = pb->params + (size_t)cell * pb->nparams;
     switch (pb->kind) {
     case ORC_ROBERTSON: FN(rhs_robertson)(prm, y, f); break;
-    case ORC_MECHANISM: FN(rhs_mechanism)(pb, prm, y, f); break;
+    case ORC_MECHANISM: FN(rhs_mechanism)(pb, prm, y, f, -1); break;
     case ORC_COSMOLOGY: FN(rhs_cosmology)(pb, prm, y, f); break;
     case ORC_LINEAR:    FN(rhs_linear)(pb, prm, y, f); break;
     }

@@ -79,6 +79,9 @@ SIGNATURES = {
     "sunb_jac": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
     "sunb_lu_solve_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "sunb_lu_solve_batched_f32": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
+    "sunb_adjoint_replay": (ctypes.c_int, [_vp, _vp]),
+    "sunb_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
+    "sunb_set_arrhenius": (ctypes.c_int, [_vp, _dp, _dp]),
     "sunb_get_lanes_per_cell": (ctypes.c_int, [_vp]),
     "sunb_get_launch_count": (ctypes.c_int64, [_vp]),
     "sunb_get_mapping": (ctypes.c_int, [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
@@ -136,12 +139,12 @@ class Integrator:
 
     def __init__(self, kind, n_cells, mech=None, table=None, n_cells_cosmo=0,
                  max_order=5, max_steps=100000, precision=FP64, lanes_per_cell=0,
-                 schedule=SCHED_QUEUE, stream=None):
+                 schedule=SCHED_QUEUE, stream=None, record_adjoint=0):
         self._keep = []
         p = _Problem()
         p.kind, p.n_cells, p.n_cells_cosmo = kind, n_cells, n_cells_cosmo
         p.max_order, p.max_steps, p.precision = max_order, max_steps, precision
-        p.lanes_per_cell, p.schedule, p.record_adjoint = lanes_per_cell, schedule, 0
+        p.lanes_per_cell, p.schedule, p.record_adjoint = lanes_per_cell, schedule, record_adjoint
         if mech is not None:
             arrs = dict(W=_cont(mech.W, np.float64), nasa=_cont(mech.nasa, np.float64),
                         react=_cont(mech.react, np.int32), prod=_cont(mech.prod, np.int32),
@@ -160,6 +163,7 @@ class Integrator:
             self._keep.append(t)
             p.table = ctypes.pointer(t)
         self.kind, self.n_cells, self.n_cells_cosmo = kind, n_cells, n_cells_cosmo
+        self.n_reactions = mech.n_reactions if mech is not None else 0
         self.n_vars = {ROBERTSON: 3, COSMOLOGY: 1}.get(kind, mech.n_vars if mech is not None else 0)
         self._stream = stream
         ctx = ctypes.c_void_p()
@@ -209,6 +213,29 @@ class Integrator:
         out = torch.empty((self.n_cells + self.n_cells_cosmo, 8), dtype=torch.int32, device="cuda")
         self.totals(out)
         return out
+
+    # -- discrete adjoint
+    def set_arrhenius(self, lnA, Ea):
+        a, e = _cont(lnA, np.float64), _cont(Ea, np.float64)
+        _check(lib().sunb_set_arrhenius(self.ctx, a.ctypes.data_as(_dp), e.ctypes.data_as(_dp)), self.ctx)
+
+    def adjoint_replay(self, y_final=None):
+        """Recompute the recorded step history with exact correctors; returns
+        (or fills) the final states of that map."""
+        import torch
+        out = torch.empty((self.n_cells, self.n_vars), dtype=torch.float64, device="cuda") \
+            if y_final is None else y_final
+        _check(lib().sunb_adjoint_replay(self.ctx, _ptr(out)), self.ctx)
+        return out
+
+    def adjoint(self, dLdy, per_cell=False):
+        """d loss / d (ln A, Ea) [M, 2] for dLdy = d loss / d y_final [C, N]."""
+        import torch
+        g = torch.empty((self.n_reactions, 2), dtype=torch.float64, device="cuda")
+        gc = torch.empty((self.n_cells, self.n_reactions, 2), dtype=torch.float64, device="cuda") \
+            if per_cell else None
+        _check(lib().sunb_adjoint(self.ctx, _ptr(dLdy.contiguous()), _ptr(g), _ptr(gc)), self.ctx)
+        return (g, gc) if per_cell else g
 
     # -- single steps of the path
     def rhs(self, y, out=None):
@@ -295,3 +322,37 @@ def from_workload(w, precision=FP64, lanes_per_cell=0, schedule=SCHED_QUEUE, max
                         schedule=schedule, max_steps=max_steps, stream=stream)
         it.set_tolerances(w["rtol"], w["atol"])
     return it
+
+
+def _autograd():
+    import torch
+
+    class _ArrheniusIntegrate(torch.autograd.Function):
+        """y_final(ln A, Ea) of a recorded integration; backward by the
+        discrete adjoint of the BDF steps (sunb_adjoint)."""
+
+        @staticmethod
+        def forward(ctx, lnA, Ea, integrator, y0, t0, tout):
+            integrator.set_arrhenius(lnA.detach().cpu().numpy(), Ea.detach().cpu().numpy())
+            y = y0.detach().clone()
+            integrator.integrate(y, t0, tout)
+            yrep = integrator.adjoint_replay()
+            ctx.integrator = integrator
+            ctx.devices = (lnA.device, Ea.device)
+            return yrep
+
+        @staticmethod
+        def backward(ctx, grad_y):
+            g = ctx.integrator.adjoint(grad_y.contiguous())
+            return g[:, 0].to(ctx.devices[0]), g[:, 1].to(ctx.devices[1]), None, None, None, None
+
+    return _ArrheniusIntegrate
+
+
+def integrate_arrhenius(lnA, Ea, integrator, y0, t0, tout):
+    """Differentiable integration: returns the final states [C, N] of the
+    exact-corrector map of the BDF steps taken from y0 over [t0, tout] with
+    Arrhenius parameters (lnA, Ea) (tensors [M]); gradients flow to lnA and
+    Ea through the discrete adjoint.  `integrator` must be a mechanism
+    Integrator created with record_adjoint > 0 and with parameters set."""
+    return _autograd().apply(lnA, Ea, integrator, y0, t0, tout)

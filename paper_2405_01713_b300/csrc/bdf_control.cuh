@@ -160,6 +160,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         h = fmin(h, span);
     }
     c.scale(V_Z1, h, V_F);
+    c.rec_init(h);
 
     double t = t0;
     int q = 1, qwait = 2, have_M = 0, force_setup = 1, nst_lastsetup = 0, have_ks = 0;
@@ -182,6 +183,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         c.set_weights(V_Z0, ctl.rtol);          // Eq. wrms: weights from y^{n-1}
         int ncf = 0, nef = 0;
         double dsm2 = 0.0, l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1], Cq = 0.0;
+        double gamma_acc = 0.0, il1_acc = 0.0;     // of the attempt that is accepted
         for (;;) {   // attempts
             c.predict(q);
             double il1;
@@ -201,6 +203,8 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 Cq = rcp(1.0 + l[1] * xi[q]);
             }
             const double gamma = h * il1;
+            gamma_acc = gamma;
+            il1_acc = il1;
             const double Cq2 = Cq * Cq;
             int fresh = 0, conv = 0, fcur = 0;   // fcur: V_F holds f(z0) already
             if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
@@ -305,7 +309,10 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
 #pragma unroll
         for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
         hist[0] = h;
-        if (last) break;
+        if (last) {
+            c.rec_accept(q, q, l, 0.0, gamma_acc, il1_acc);
+            break;
+        }
 
         qwait--;
         const double l1 = l[1];
@@ -338,6 +345,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         }
         if (eta < ETA_THRESH) { eta = 1.0; newq = q; }
         else eta = fmin(eta, etamax);
+        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma_acc, il1_acc);
         if (newq == q + 1) c.order_increase(q, l, inv[q]);
         else if (newq == q - 1) {
             double e[QMAX + 1];

@@ -44,7 +44,8 @@ struct MechTabOffsets {
 // Per-cell shared-memory layout (byte offsets from the cell's base).
 struct CellLayout {
     int NP;            // padded vector length
-    int vec, mat, perm, xs, sp, rq, dq, bytes;   // xs holds 2N MT (solve scratch, reciprocal pivots)
+    int vec, mat, perm, xs, sp, rq, dq, pm, bytes;   // xs: 2N MT (solve scratch, reciprocal pivots);
+                                                     // pm: 36 + K + 1 doubles (adjoint map and scratch)
 };
 
 struct MechTab {
@@ -90,6 +91,12 @@ struct Grp {
     {
 #pragma unroll
         for (int o = L / 2; o > 0; o >>= 1) v += __shfl_xor_sync(mask, v, o);
+        return v;
+    }
+    __device__ __forceinline__ double max(double v) const
+    {
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(mask, v, o));
         return v;
     }
     __device__ __forceinline__ void sync() const { __syncwarp(mask); }
@@ -185,6 +192,37 @@ __device__ void lu_solve(const Grp<L> &g, const MT *mat, int N, const int32_t *p
     g.sync();
 }
 
+// Solve M^T x = b with the factors of lu_factor (P M = L U, so
+// M^T = U^T L^T P): U^T w = b, L^T v = w, x_perm[i] = v_i.  In place in b.
+template <int L>
+__device__ void lu_solve_t(const Grp<L> &g, const double *mat, int N, const int32_t *perm,
+                           const double *dinv, double *xs, double *b)
+{
+    for (int i = g.lane; i < N; i += L) xs[i] = b[i];
+    g.sync();
+    for (int k = 0; k < N; ++k) {
+        const double wk = xs[k] * dinv[k];
+        for (int i = k + 1 + g.lane; i < N; i += L) xs[i] -= mat[k * N + i] * wk;
+        g.sync();
+        if (g.lane == 0) xs[k] = wk;
+        g.sync();
+    }
+    for (int k = N - 1; k > 0; --k) {
+        const double vk = xs[k];
+        for (int i = g.lane; i < k; i += L) xs[i] -= mat[k * N + i] * vk;
+        g.sync();
+    }
+    for (int i = g.lane; i < N; i += L) b[perm[i]] = xs[i];
+    g.sync();
+}
+
+// Header and record sizes (doubles) of a cell's adjoint tape: the header is
+// [count, h0, overflow, 5 spare, y0 (N)]; a record is y_n (N), the column
+// map P (6 x 6, row = output column), the update vector c (6), gamma, 1/l_1,
+// q, q_out.
+__host__ __device__ __forceinline__ int tape_header(int N) { return 8 + N; }
+__host__ __device__ __forceinline__ int tape_record(int N) { return N + 46; }
+
 template <int L, typename MT>
 struct GroupCell {
     Grp<L> g;
@@ -201,6 +239,12 @@ struct GroupCell {
     MT *dq;                                             // [6M] gamma dq_j/dC at each position
     double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
     double *yg;
+    // discrete-adjoint recording (null tape: no recording)
+    double *tape = nullptr;
+    int tape_cap = 0, rec_count = 0;
+    double *Pm;          // [36] column map accumulated since the last accepted step
+    double *wmu;         // [K+1] adjoint scratch (W_k mu_k, zero sentinel)
+    double last_rho, last_cpm, last_T;
 
     __device__ __forceinline__ double *V(int s) const { return vec + s * NP; }
 
@@ -219,8 +263,58 @@ struct GroupCell {
         dq = reinterpret_cast<MT *>(base + lay.dq);
         dqdT = reinterpret_cast<double *>(base + lay.dq + ((6 * M * (int)sizeof(MT) + 15) & ~15));
         uq = dqdT + M;
-        if (g.lane == 0) { C[K] = 1.0; eg[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; }
+        Pm = reinterpret_cast<double *>(base + lay.pm);
+        wmu = Pm + 36;
+        if (g.lane == 0) { C[K] = 1.0; eg[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; wmu[K] = 0.0; }
         g.sync();
+    }
+
+    // ---------------- adjoint tape ----------------
+    __device__ void rec_reset_map()
+    {
+        for (int i = g.lane; i < 36; i += L) Pm[i] = (i % 7 == 0) ? 1.0 : 0.0;
+        g.sync();
+    }
+    __device__ void rec_init(double h0)
+    {
+        if (!tape) return;
+        const double *z0 = V(V_Z0);
+        for (int i = g.lane; i < N; i += L) tape[8 + i] = z0[i];
+        if (g.lane == 0) { tape[0] = 0.0; tape[1] = h0; tape[2] = 0.0; }
+        rec_count = 0;
+        rec_reset_map();
+    }
+    // one accepted step: y_n (= z0 after the correction), the map, the
+    // update vector (with the terms of an order increase), gamma, 1/l_1
+    __device__ void rec_accept(int q, int qo, const double *l, double inv_xi, double gamma, double il1)
+    {
+        if (!tape) return;
+        if (rec_count >= tape_cap) {
+            if (g.lane == 0) tape[2] = 1.0;
+            return;
+        }
+        double *r = tape + tape_header(N) + (size_t)rec_count * tape_record(N);
+        const double *z0 = V(V_Z0);
+        for (int i = g.lane; i < N; i += L) r[i] = z0[i];
+        for (int i = g.lane; i < 36; i += L) r[N + i] = Pm[i];
+        if (g.lane == 0) {
+            double c[6];
+#pragma unroll
+            for (int j = 0; j < 6; ++j) {
+                c[j] = (j <= q) ? l[j] : 0.0;
+                if (qo == q + 1 && j >= 1 && j <= q + 1) c[j] += l[j - 1] * inv_xi;
+            }
+#pragma unroll
+            for (int j = 0; j < 6; ++j) r[N + 36 + j] = c[j];
+            r[N + 42] = gamma;
+            r[N + 43] = il1;
+            r[N + 44] = (double)q;
+            r[N + 45] = (double)qo;
+            tape[0] = (double)(rec_count + 1);
+        }
+        ++rec_count;
+        g.sync();
+        rec_reset_map();
     }
 
     // ---------------- vector operations (lane-strided over N) ----------------
@@ -324,6 +418,11 @@ struct GroupCell {
 #pragma unroll
             for (int j = 1; j <= QMAX; ++j) if (j <= q) vec[j * NP + i] *= f[j];
         }
+        if (tape)
+            for (int i = g.lane; i < 6; i += L) {
+#pragma unroll
+                for (int j = 1; j <= QMAX; ++j) if (j <= q) Pm[j * 6 + i] *= f[j];
+            }
         g.sync();
     }
     __device__ __forceinline__ void correct(int q, const double *l)
@@ -356,6 +455,13 @@ struct GroupCell {
             for (int j = 1; j < QMAX; ++j) if (j < q) vec[j * NP + i] -= e[j - 1] * zq;
             vec[q * NP + i] = 0.0;
         }
+        if (tape)
+            for (int i = g.lane; i < 6; i += L) {
+                const double pq = Pm[q * 6 + i];
+#pragma unroll
+                for (int j = 1; j < QMAX; ++j) if (j < q) Pm[j * 6 + i] -= e[j - 1] * pq;
+                Pm[q * 6 + i] = 0.0;
+            }
         g.sync();
     }
     __device__ __forceinline__ void restart(double h)
@@ -474,6 +580,9 @@ struct GroupCell {
         cpm = g.sum(cpm);
         const double fT = -T * hw * rcp(rho * cpm);
         if (g.lane == 0) f[K] = fT;
+        last_rho = rho;
+        last_cpm = cpm;
+        last_T = T;
         g.sync();
         if (!JAC) return 1;
 

@@ -98,6 +98,9 @@ struct ThreadCell {
     double atol[N];
     double *yg;   // this cell's state in global memory
 
+    __device__ __forceinline__ void rec_init(double) {}
+    __device__ __forceinline__ void rec_accept(int, int, const double *, double, double, double) {}
+
     __device__ __forceinline__ void load_y(int s)
     {
 #pragma unroll

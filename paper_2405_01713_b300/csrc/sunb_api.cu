@@ -78,6 +78,10 @@ struct MechArgs {
     CoolArgs cool;
     double atol_cosmo;
     int cool_smem_off;
+    // discrete-adjoint tape (null: not recorded)
+    double *tape;
+    long long tape_stride;
+    int tape_cap;
 };
 
 __device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned char *src, int bytes)
@@ -142,6 +146,8 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
         c.P = a.p_mech[cell];
         c.invP = rcp(c.P);
         c.yg = a.y_mech + cell * c.N;
+        c.tape = a.tape ? a.tape + cell * a.tape_stride : nullptr;
+        c.tape_cap = a.tape_cap;
         CellStats st;
         bdf_cell(c, a.ctl, st);
         if (c.g.lane == 0) write_stats(a.stats_mech, a.status_mech, cell, st);
@@ -293,6 +299,227 @@ __global__ void __launch_bounds__(128) lu_batched_kernel(int n, long long batch,
     }
 }
 
+
+// ---------------------------------------------------------------- adjoint
+// Discrete adjoint of the recorded forward map (one warp per cell, FP64).
+// Replay: recompute the step history from the tape header (y0, h0) with each
+// corrector solved by full Newton (fresh analytic Jacobian per iteration) to
+// rounding level, overwriting the tape's states with these exact ones.
+// Reverse: lam (the adjoint of the Nordsieck array) is carried back through
+// each step's update, corrector (mu = (I - gamma J(y_n))^{-T} lam_Delta),
+// prediction and column map, accumulating gamma (df/dtheta)^T mu for
+// theta = (ln A_j, Ea_j): <df/dlnA_j, mu> = (q_j/rho)(sum_k nu_kj W_k mu_k
+// - T dH_j mu_T / cpm), df/dEa_j = -df/dlnA_j / (Rc T).
+struct AdjArgs {
+    MechArgs m;
+    const double *dLdy;     // [C, N]
+    double *yrep;           // [C, N] replayed final states (nullable)
+    double *gcells;         // [C, M, 2]
+    long long n;
+};
+
+template <int L>
+__device__ void adj_theta(GroupCell<L, double> &c, const double *mu, double scale, double *g)
+{
+    const int K = c.K, M = c.M;
+    for (int k = c.g.lane; k < K; k += L) c.wmu[k] = c.tb.W[k] * mu[k];
+    c.g.sync();
+    const double T = c.last_T, muT = mu[K];
+    const double a = scale / c.last_rho, b = T * muT / c.last_cpm;
+    const double iRT = rcp(RC * T);
+    for (int j = c.g.lane; j < M; j += L) {
+        const uint32_t u = c.tb.ridx[2 * j], v = c.tb.ridx[2 * j + 1];
+        const int r0 = u & 0xff, r1 = (u >> 8) & 0xff, r2 = (u >> 16) & 0xff, p0 = u >> 24;
+        const int p1 = v & 0xff, p2 = (v >> 8) & 0xff;
+        const double sw = (c.wmu[p0] + c.wmu[p1] + c.wmu[p2]) - (c.wmu[r0] + c.wmu[r1] + c.wmu[r2]);
+        const double dH = (c.hRT[p0] + c.hRT[p1] + c.hRT[p2]) - (c.hRT[r0] + c.hRT[r1] + c.hRT[r2]);
+        const double d = a * c.q[j] * (sw - b * dH);
+        g[2 * j] += d;
+        g[2 * j + 1] -= d * iRT;
+    }
+    c.g.sync();
+}
+
+template <int L>
+__device__ void adj_bind(GroupCell<L, double> &c, unsigned char *smem, const MechArgs &m, int gid)
+{
+    c.g.lane = threadIdx.x % L;
+    c.g.mask = group_mask<L>();
+    c.tb = mech_tab_at(smem, m.off);
+    c.N = m.off.N; c.K = m.off.K; c.M = m.off.M;
+    c.invN = m.invN;
+    c.bind(smem + m.off.bytes + gid * m.lay.bytes, m.lay);
+    c.tape = nullptr;
+}
+
+__global__ void __launch_bounds__(128) adjoint_replay_kernel(const AdjArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_bytes(smem, a.m.tab, a.m.off.bytes);
+    __syncthreads();
+    constexpr int L = 32;
+    GroupCell<L, double> c;
+    adj_bind<L>(c, smem, a.m, threadIdx.x / L);
+    const int N = c.N, H = tape_header(N), R = tape_record(N);
+    for (;;) {
+        const long long cell = grab_group(a.m.queue, c.g.lane, c.g.mask, L);
+        if (cell >= a.n) break;
+        double *tp = a.m.tape + cell * a.m.tape_stride;
+        c.P = a.m.p_mech[cell];
+        c.invP = rcp(c.P);
+        const int count = (int)tp[0];
+        const bool bad = tp[2] != 0.0;
+        double *z0 = c.V(V_Z0), *y = c.V(V_Y), *f = c.V(V_F), *d = c.V(V_DEL);
+        for (int i = c.g.lane; i < N; i += L) y[i] = tp[8 + i];
+        c.g.sync();
+        c.rhs(V_Y, V_F);
+        for (int i = c.g.lane; i < N; i += L) {
+            z0[i] = y[i];
+            c.vec[c.NP + i] = tp[1] * f[i];
+            for (int j = 2; j <= QMAX; ++j) c.vec[j * c.NP + i] = 0.0;
+        }
+        c.g.sync();
+        for (int r = 0; r < count && !bad; ++r) {
+            double *rec = tp + H + (long long)r * R;
+            const double *Pm = rec + N, *cv = rec + N + 36;
+            const double gamma = rec[N + 42], il1 = rec[N + 43];
+            const int q = (int)rec[N + 44], qo = (int)rec[N + 45];
+            for (int i = c.g.lane; i < N; i += L) {      // Z_pre = P Z
+                double zin[6], zo[6];
+                for (int j = 0; j < 6; ++j) zin[j] = c.vec[j * c.NP + i];
+                for (int o = 0; o < 6; ++o) {
+                    double acc = 0.0;
+                    for (int j = 0; j < 6; ++j) acc += Pm[o * 6 + j] * zin[j];
+                    zo[o] = acc;
+                }
+                for (int o = 0; o < 6; ++o) c.vec[o * c.NP + i] = zo[o];
+                y[i] = rec[i];
+            }
+            c.g.sync();
+            c.predict(q);
+            for (int it = 0; it < 12; ++it) {             // full Newton, exact J
+                c.template eval<true>(V_Y, V_F, gamma);
+                if (!c.factor()) break;
+                for (int i = c.g.lane; i < N; i += L)
+                    d[i] = -(y[i] - gamma * f[i] - (z0[i] - il1 * c.vec[c.NP + i]));
+                c.g.sync();
+                c.solve(V_DEL);
+                double worst = 0.0;           // converged in every component
+                for (int i = c.g.lane; i < N; i += L) {
+                    y[i] += d[i];
+                    worst = fmax(worst, fabs(d[i]) - (1e-13 * fabs(y[i]) + 1e-30));
+                }
+                worst = c.g.max(worst);
+                c.g.sync();
+                if (worst <= 0.0) break;
+            }
+            for (int i = c.g.lane; i < N; i += L) {
+                rec[i] = y[i];
+                const double del = y[i] - z0[i];
+                for (int j = 0; j < 6; ++j) {
+                    const double zj = (j <= q) ? c.vec[j * c.NP + i] : 0.0;
+                    c.vec[j * c.NP + i] = (j <= qo) ? zj + cv[j] * del : 0.0;
+                }
+            }
+            c.g.sync();
+        }
+        if (a.yrep)
+            for (int i = c.g.lane; i < N; i += L) a.yrep[cell * N + i] = bad ? __longlong_as_double(0x7ff8000000000000LL) : z0[i];
+        c.g.sync();
+    }
+}
+
+__global__ void __launch_bounds__(128) adjoint_reverse_kernel(const AdjArgs a)
+{
+    extern __shared__ __align__(16) unsigned char smem[];
+    stage_bytes(smem, a.m.tab, a.m.off.bytes);
+    __syncthreads();
+    constexpr int L = 32;
+    GroupCell<L, double> c;
+    adj_bind<L>(c, smem, a.m, threadIdx.x / L);
+    const int N = c.N, M = c.M, H = tape_header(N), R = tape_record(N);
+    for (;;) {
+        const long long cell = grab_group(a.m.queue, c.g.lane, c.g.mask, L);
+        if (cell >= a.n) break;
+        const double *tp = a.m.tape + cell * a.m.tape_stride;
+        double *g = a.gcells + cell * 2 * M;
+        for (int j = c.g.lane; j < 2 * M; j += L) g[j] = 0.0;
+        c.P = a.m.p_mech[cell];
+        c.invP = rcp(c.P);
+        const int count = (int)tp[0];
+        const bool bad = tp[2] != 0.0;
+        double *lam = c.vec, *y = c.V(V_Y), *ld = c.V(V_DEL);
+        for (int i = c.g.lane; i < N; i += L) {
+            lam[i] = a.dLdy[cell * N + i];
+            for (int j = 1; j < 6; ++j) lam[j * c.NP + i] = 0.0;
+        }
+        c.g.sync();
+        for (int r = count - 1; r >= 0 && !bad; --r) {
+            const double *rec = tp + H + (long long)r * R;
+            const double *Pm = rec + N, *cv = rec + N + 36;
+            const double gamma = rec[N + 42], il1 = rec[N + 43];
+            const int q = (int)rec[N + 44], qo = (int)rec[N + 45];
+            for (int i = c.g.lane; i < N; i += L) {
+                double s = 0.0;
+                for (int j = 0; j <= qo; ++j) s += cv[j] * lam[j * c.NP + i];
+                ld[i] = s;
+                for (int j = q + 1; j < 6; ++j) lam[j * c.NP + i] = 0.0;
+                lam[i] -= s;
+                y[i] = rec[i];
+            }
+            c.g.sync();
+            c.template eval<true>(V_Y, V_F, gamma);       // M = I - gamma J(y_n)
+            c.factor();
+            lu_solve_t<L>(c.g, c.mat, N, c.perm, c.dinv, c.xs, ld);   // mu
+            adj_theta<L>(c, ld, gamma, g);
+            for (int i = c.g.lane; i < N; i += L) {
+                lam[i] += ld[i];
+                lam[c.NP + i] -= il1 * ld[i];
+                double l6[6], o6[6];
+                for (int j = 0; j < 6; ++j) l6[j] = lam[j * c.NP + i];
+                for (int k = q - 1; k >= 0; --k)              // prediction, transposed
+                    for (int j = k + 1; j <= q; ++j) l6[j] += l6[j - 1];
+                for (int aa = 0; aa < 6; ++aa) {              // column map, transposed
+                    double acc = 0.0;
+                    for (int o = 0; o < 6; ++o) acc += Pm[o * 6 + aa] * l6[o];
+                    o6[aa] = acc;
+                }
+                for (int j = 0; j < 6; ++j) lam[j * c.NP + i] = o6[j];
+            }
+            c.g.sync();
+        }
+        // z1 = h0 f(y0)
+        for (int i = c.g.lane; i < N; i += L) y[i] = tp[8 + i];
+        c.g.sync();
+        c.rhs(V_Y, V_F);
+        if (!bad) adj_theta<L>(c, lam + c.NP, tp[1], g);
+        else
+            for (int j = c.g.lane; j < 2 * M; j += L) g[j] = __longlong_as_double(0x7ff8000000000000LL);
+        c.g.sync();
+    }
+}
+
+// Deterministic sum over cells: fixed chunks, then the chunk sums in order.
+__global__ void grad_partial_kernel(const double *gcells, long long n, int len, int chunk, double *part)
+{
+    const int t = threadIdx.x + blockIdx.y * blockDim.x;
+    if (t >= len) return;
+    const long long c0 = (long long)blockIdx.x * chunk;
+    const long long c1 = c0 + chunk < n ? c0 + chunk : n;
+    double s = 0.0;
+    for (long long cc = c0; cc < c1; ++cc) s += gcells[cc * len + t];
+    part[(long long)blockIdx.x * len + t] = s;
+}
+
+__global__ void grad_final_kernel(const double *part, int nchunks, int len, double *grad)
+{
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= len) return;
+    double s = 0.0;
+    for (int k = 0; k < nchunks; ++k) s += part[(long long)k * len + t];
+    grad[t] = s;
+}
+
 struct DevTotals {
     unsigned long long sum[6];
     int max_nst;
@@ -358,6 +585,12 @@ struct sunb_ctx {
     double *d_ybuf = nullptr;
     int32_t *d_sbuf = nullptr;
     double *d_tune = nullptr;        // autotuning sample (copy of the first cells)
+    double *d_tape = nullptr;        // adjoint tapes, one per mechanism cell
+    long long tape_stride = 0;
+    int tape_cap = 0;
+    bool replayed = false;           // tapes hold exact states of the last integration
+    double *d_gcells = nullptr;      // per-cell gradients [C, M, 2]
+    double *d_gpart = nullptr;       // partial sums of the gradient reduction
     long long tune_cells = 0;
     float tune_ms[3][2] = {{0}};     // per L = 8/16/32: trial ms and trial cells
     long long launches = 0;
@@ -488,6 +721,7 @@ static CellLayout make_layout(int N, int K, int M, int mt)
     l.sp = take(8 * (4 * (K + 1) + 4 * K));
     l.rq = take(8 * M);
     l.dq = take(align16(mt * 6 * M) + 8 * 2 * M);   // dq (MT), then dq/dT and u terms (FP64)
+    l.pm = take(8 * (36 + K + 1));                  // adjoint column map and scratch
     l.bytes = off;
     return l;
 }
@@ -561,6 +795,9 @@ static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int3
     a.ctl.max_steps = ctx->max_steps;
     a.ctl.max_order = ctx->max_order;
     a.queue = ctx->d_queue;
+    a.tape = ctx->d_tape;
+    a.tape_stride = ctx->tape_stride;
+    a.tape_cap = ctx->tape_cap;
     const bool mixed = ctx->kind == SUNB_MIXED;
     a.n_mech = ctx->C;
     a.y_mech = y ? y + (mixed ? ctx->Cc : 0) : nullptr;
@@ -592,6 +829,7 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
         a.y_mech = y;
         a.p_mech = ctx->params + (cosmo ? 2 * ctx->Cc : 0);
         a.n_cosmo = 0;
+        a.tape = nullptr;
     }
     if (cosmo) {   // mechanism tables, cooling table, then the cells
         a.cool_smem_off = ctx->off.bytes;
@@ -609,7 +847,7 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
         const int shift = cool_bytes(ctx);
         // GroupCell::bind takes offsets from (tables + gid * cell bytes); shift every field
         lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
-        lay.sp += shift; lay.rq += shift; lay.dq += shift;
+        lay.sp += shift; lay.rq += shift; lay.dq += shift; lay.pm += shift;
         a.lay = lay;
         a.lay.bytes = ctx->lay.bytes;
     }
@@ -734,6 +972,34 @@ static int eval_config(sunb_ctx *ctx, MechArgs &a, int &bytes)
     return SUNB_SUCCESS;
 }
 
+
+static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
+{
+    AdjArgs a{};
+    a.m = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
+    a.m.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
+    a.m.cells_per_cta = 4;
+    a.dLdy = dLdy;
+    a.yrep = yrep;
+    a.gcells = ctx->d_gcells;
+    a.n = ctx->C;
+    int optin = 0;
+    CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
+    while (a.m.cells_per_cta > 1 && ctx->off.bytes + a.m.cells_per_cta * a.m.lay.bytes > optin) --a.m.cells_per_cta;
+    const int bytes = ctx->off.bytes + a.m.cells_per_cta * a.m.lay.bytes;
+    if (bytes > optin) return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for the adjoint kernels");
+    void *k = mode == 0 ? (void *)adjoint_replay_kernel : (void *)adjoint_reverse_kernel;
+    CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+    int occ = 1;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * a.m.cells_per_cta, bytes));
+    CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
+    void *args[] = {&a};
+    CU(cudaLaunchKernel(k, dim3(ctx->num_sms * std::max(1, occ)), dim3(32 * a.m.cells_per_cta), args, bytes,
+                        ctx->stream));
+    ctx->launches++;
+    return SUNB_SUCCESS;
+}
+
 extern "C" {
 
 const char *sunb_version(void) { return "sunb 0.1 (sm_103a)"; }
@@ -762,7 +1028,8 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
     if (ctx->max_steps < 1) { fail(ctx, SUNB_ILL_INPUT, "max_steps must be positive"); return bail(SUNB_ILL_INPUT); }
     if (prob->precision != SUNB_FP64 && prob->precision != SUNB_MIXED32) { fail(ctx, SUNB_ILL_INPUT, "unknown precision"); return bail(SUNB_ILL_INPUT); }
     if (prob->schedule != SUNB_SCHED_QUEUE && prob->schedule != SUNB_SCHED_STATIC) { fail(ctx, SUNB_ILL_INPUT, "unknown schedule"); return bail(SUNB_ILL_INPUT); }
-    if (prob->record_adjoint) { fail(ctx, SUNB_ILL_INPUT, "record_adjoint is not supported by this build"); return bail(SUNB_ILL_INPUT); }
+    if (prob->record_adjoint < 0 || prob->record_adjoint > (1 << 20)) { fail(ctx, SUNB_ILL_INPUT, "record_adjoint must be 0..2^20 steps"); return bail(SUNB_ILL_INPUT); }
+    if (prob->record_adjoint && prob->kind != SUNB_MECHANISM) { fail(ctx, SUNB_ILL_INPUT, "the adjoint is available for SUNB_MECHANISM contexts"); return bail(SUNB_ILL_INPUT); }
     const int lpc = prob->lanes_per_cell;
     if (lpc != 0 && lpc != 8 && lpc != 16 && lpc != 32) { fail(ctx, SUNB_ILL_INPUT, "lanes_per_cell must be 0, 8, 16 or 32"); return bail(SUNB_ILL_INPUT); }
     int rc;
@@ -810,6 +1077,17 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
         int L = lpc ? lpc : (ctx->off.N > 32 ? 32 : 16);
         ctx->autotune = lpc == 0;
         if ((rc = configure_mech(ctx, L)) != SUNB_SUCCESS) return bail(rc);
+        if (prob->record_adjoint) {
+            ctx->tape_cap = prob->record_adjoint;
+            ctx->tape_stride = tape_header(ctx->N) + (long long)ctx->tape_cap * tape_record(ctx->N);
+            if (cudaMalloc(&ctx->d_tape, 8 * (size_t)ctx->tape_stride * ctx->C) != cudaSuccess ||
+                cudaMalloc(&ctx->d_gcells, 8 * 2 * (size_t)ctx->off.M * ctx->C) != cudaSuccess ||
+                cudaMalloc(&ctx->d_gpart, 8 * 2 * (size_t)ctx->off.M * 1024) != cudaSuccess) {
+                fail(ctx, SUNB_MEM_FAIL, "cudaMalloc adjoint tapes");
+                return bail(SUNB_MEM_FAIL);
+            }
+            cudaMemset(ctx->d_tape, 0, 8 * (size_t)ctx->tape_stride * ctx->C);
+        }
         if (ctx->autotune) {
             // eight waves of the densest mapping
             long long most = 0;
@@ -839,6 +1117,9 @@ int sunb_destroy(sunb_ctx *ctx)
     cudaFree(ctx->d_ybuf);
     cudaFree(ctx->d_sbuf);
     cudaFree(ctx->d_tune);
+    cudaFree(ctx->d_tape);
+    cudaFree(ctx->d_gcells);
+    cudaFree(ctx->d_gpart);
     delete ctx;
     return SUNB_SUCCESS;
 }
@@ -879,6 +1160,7 @@ int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t
         return fail(ctx, SUNB_ILL_INPUT, "need finite t0 <= tout");
     if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)
         return launch_thread(ctx, dev_y, t0, tout, dev_status);
+    ctx->replayed = false;
     if (ctx->autotune && !ctx->tuned && ctx->tune_cells > 0 && tout > t0) {
         const int rc = autotune(ctx, dev_y, t0, tout);
         if (rc != SUNB_SUCCESS) return rc;
@@ -998,6 +1280,60 @@ int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *d
                               int32_t *dev_info, void *stream)
 {
     return lu_batched<float>(n, batch, dev_A, dev_piv, dev_b, dev_info, stream);
+}
+
+
+int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!ctx->d_tape) return fail(ctx, SUNB_NO_RECORD, "context created without record_adjoint");
+    if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
+    const int rc = adj_launch(ctx, 0, nullptr, dev_y_final);
+    if (rc == SUNB_SUCCESS) ctx->replayed = true;
+    return rc;
+}
+
+int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double *dev_grad_cells)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!ctx->d_tape) return fail(ctx, SUNB_NO_RECORD, "context created without record_adjoint");
+    if (!dev_dLdy || !dev_grad) return fail(ctx, SUNB_ILL_INPUT, "dLdy and grad must not be NULL");
+    if (!ctx->replayed) {
+        const int rc = sunb_adjoint_replay(ctx, nullptr);
+        if (rc != SUNB_SUCCESS) return rc;
+    }
+    int rc = adj_launch(ctx, 1, dev_dLdy, nullptr);
+    if (rc != SUNB_SUCCESS) return rc;
+    const int len = 2 * ctx->off.M;
+    const long long chunk = std::max<long long>(1, (ctx->C + 1023) / 1024);
+    const int nchunks = (int)((ctx->C + chunk - 1) / chunk);
+    dim3 grid(nchunks, (len + 255) / 256);
+    grad_partial_kernel<<<grid, 256, 0, ctx->stream>>>(ctx->d_gcells, ctx->C, len, (int)chunk, ctx->d_gpart);
+    grad_final_kernel<<<(len + 255) / 256, 256, 0, ctx->stream>>>(ctx->d_gpart, nchunks, len, dev_grad);
+    CU(cudaGetLastError());
+    ctx->launches += 2;
+    if (dev_grad_cells)
+        CU(cudaMemcpyAsync(dev_grad_cells, ctx->d_gcells, 8 * (size_t)len * ctx->C, cudaMemcpyDeviceToDevice,
+                           ctx->stream));
+    return SUNB_SUCCESS;
+}
+
+int sunb_set_arrhenius(sunb_ctx *ctx, const double *host_lnA, const double *host_Ea)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!ctx->d_tab) return fail(ctx, SUNB_ILL_INPUT, "not a mechanism context");
+    if (!host_lnA || !host_Ea) return fail(ctx, SUNB_ILL_INPUT, "lnA and Ea must not be NULL");
+    double *rp = reinterpret_cast<double *>(ctx->blob.data() + ctx->off.rpar);
+    for (int j = 0; j < ctx->off.M; ++j) {
+        if (!std::isfinite(host_lnA[j]) || !std::isfinite(host_Ea[j]))
+            return fail(ctx, SUNB_ILL_INPUT, "Arrhenius parameters must be finite");
+        rp[3 * j] = host_lnA[j];
+        rp[3 * j + 2] = host_Ea[j] / RC;
+    }
+    CU(cudaMemcpyAsync(ctx->d_tab + ctx->off.rpar, rp, 8 * 3 * ctx->off.M, cudaMemcpyHostToDevice, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    ctx->replayed = false;
+    return SUNB_SUCCESS;
 }
 
 int sunb_get_lanes_per_cell(const sunb_ctx *ctx) { return ctx ? ctx->L : 0; }

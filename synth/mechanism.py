@@ -92,7 +92,11 @@ def make_mechanism(n_species, n_reactions, seed):
     react = -np.ones((M, 3), dtype=np.int32)
     prod = -np.ones((M, 3), dtype=np.int32)
     j = 0
+    tries = 0
     while j < M:
+        tries += 1
+        if tries > 1000 * M + 10000:
+            raise ValueError("no balanced reactions can be drawn for these species")
         u = st.uniform(1)[0]
         nr = 1 if u < 0.3 else (2 if u < 0.85 else 3)
         rs = tuple(sorted(st.integers(nr, K).tolist()))
