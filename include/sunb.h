@@ -196,6 +196,19 @@ int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double
  * mechanism context; synchronises the context's stream. */
 int sunb_set_arrhenius(sunb_ctx *ctx, const double *host_lnA, const double *host_Ea);
 
+/* CUDA graph of outer steps: sunb_graph_capture builds (without running
+ * it) a graph of nsteps consecutive outer steps on dev_y, [t0 + k dt,
+ * t0 + (k+1) dt] for k < nsteps, each a cold start as in sunb_integrate
+ * (queue reset, then the persistent kernel); the autotuner's trials, if
+ * pending, run first (synchronously).  sunb_graph_launch re-times the
+ * captured steps to start at t0 (kernel-node parameter updates, no
+ * re-capture) and launches the graph on the context's stream; dev_y and
+ * dev_status stay those given at capture.  Not available with
+ * record_adjoint.  A new capture replaces the previous graph. */
+int sunb_graph_capture(sunb_ctx *ctx, double *dev_y, double t0, double dt, int32_t nsteps,
+                       int32_t *dev_status);
+int sunb_graph_launch(sunb_ctx *ctx, double t0);
+
 /* Lanes per mechanism cell chosen by the context (autotuned when asked). */
 int sunb_get_lanes_per_cell(const sunb_ctx *ctx);
 

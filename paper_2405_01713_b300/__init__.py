@@ -82,6 +82,8 @@ SIGNATURES = {
     "sunb_adjoint_replay": (ctypes.c_int, [_vp, _vp]),
     "sunb_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sunb_set_arrhenius": (ctypes.c_int, [_vp, _dp, _dp]),
+    "sunb_graph_capture": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _vp]),
+    "sunb_graph_launch": (ctypes.c_int, [_vp, ctypes.c_double]),
     "sunb_get_lanes_per_cell": (ctypes.c_int, [_vp]),
     "sunb_get_launch_count": (ctypes.c_int64, [_vp]),
     "sunb_get_mapping": (ctypes.c_int, [_vp, _ip, _ip, _ip, ctypes.POINTER(ctypes.c_float)]),
@@ -213,6 +215,15 @@ class Integrator:
         out = torch.empty((self.n_cells + self.n_cells_cosmo, 8), dtype=torch.int32, device="cuda")
         self.totals(out)
         return out
+
+    # -- CUDA graph of outer steps
+    def graph_capture(self, y, t0, dt, nsteps, status=None):
+        """Capture nsteps outer steps of length dt on y (kept by the graph)."""
+        self._graph_y = (y, status)
+        _check(lib().sunb_graph_capture(self.ctx, _ptr(y), t0, dt, nsteps, _ptr(status)), self.ctx)
+
+    def graph_launch(self, t0):
+        _check(lib().sunb_graph_launch(self.ctx, t0), self.ctx)
 
     # -- discrete adjoint
     def set_arrhenius(self, lnA, Ea):

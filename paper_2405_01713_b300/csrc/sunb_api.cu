@@ -590,6 +590,16 @@ struct sunb_ctx {
     int tape_cap = 0;
     bool replayed = false;           // tapes hold exact states of the last integration
     double *d_gcells = nullptr;      // per-cell gradients [C, M, 2]
+    // CUDA graph of captured outer steps
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t graph_exec = nullptr;
+    std::vector<cudaGraphNode_t> graph_kernels;
+    std::vector<MechArgs> graph_margs;
+    std::vector<ThreadArgs> graph_targs;
+    void *graph_func = nullptr;
+    dim3 graph_grid, graph_block;
+    int graph_smem = 0;
+    double graph_dt = 0.0;
     double *d_gpart = nullptr;       // partial sums of the gradient reduction
     long long tune_cells = 0;
     float tune_ms[3][2] = {{0}};     // per L = 8/16/32: trial ms and trial cells
@@ -1000,6 +1010,42 @@ static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
     return SUNB_SUCCESS;
 }
 
+
+// Kernel configuration of one outer step (the same choice as launch_mech /
+// launch_thread), for the graph builder.
+static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status, void **func,
+                       dim3 &grid, dim3 &block, int &smem, MechArgs &ma, ThreadArgs &ta)
+{
+    if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY) {
+        ta = thread_args(ctx, y, t0, tout, status);
+        *func = ctx->kind == SUNB_ROBERTSON ? (void *)thread_kernel<RobertsonProblem>
+                                            : (void *)thread_kernel<CosmologyProblem>;
+        int occ = 0;
+        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, *func, 256, 0));
+        const long long want = (ctx->C + 255) / 256;
+        grid = dim3((unsigned)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ))));
+        block = dim3(256);
+        smem = 0;
+        return SUNB_SUCCESS;
+    }
+    const bool cosmo = ctx->kind == SUNB_MIXED;
+    ma = mech_args(ctx, y, t0, tout, status);
+    if (cosmo) {
+        const int shift = cool_bytes(ctx);
+        CellLayout lay = ctx->lay;
+        lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
+        lay.sp += shift; lay.rq += shift; lay.dq += shift; lay.pm += shift;
+        ma.lay = lay;
+        ma.lay.bytes = ctx->lay.bytes;
+        ma.cool_smem_off = ctx->off.bytes;
+    }
+    *func = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
+    smem = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0) + ctx->cells_per_cta * ctx->lay.bytes;
+    grid = dim3(ctx->num_sms * ctx->ctas_per_sm);
+    block = dim3(ctx->cells_per_cta * ctx->L);
+    return SUNB_SUCCESS;
+}
+
 extern "C" {
 
 const char *sunb_version(void) { return "sunb 0.1 (sm_103a)"; }
@@ -1120,6 +1166,8 @@ int sunb_destroy(sunb_ctx *ctx)
     cudaFree(ctx->d_tape);
     cudaFree(ctx->d_gcells);
     cudaFree(ctx->d_gpart);
+    if (ctx->graph_exec) cudaGraphExecDestroy(ctx->graph_exec);
+    if (ctx->graph) cudaGraphDestroy(ctx->graph);
     delete ctx;
     return SUNB_SUCCESS;
 }
@@ -1333,6 +1381,82 @@ int sunb_set_arrhenius(sunb_ctx *ctx, const double *host_lnA, const double *host
     CU(cudaMemcpyAsync(ctx->d_tab + ctx->off.rpar, rp, 8 * 3 * ctx->off.M, cudaMemcpyHostToDevice, ctx->stream));
     CU(cudaStreamSynchronize(ctx->stream));
     ctx->replayed = false;
+    return SUNB_SUCCESS;
+}
+
+
+int sunb_graph_capture(sunb_ctx *ctx, double *dev_y, double t0, double dt, int32_t nsteps,
+                       int32_t *dev_status)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_y || nsteps < 1 || nsteps > 4096 || !(dt > 0.0) || !std::isfinite(t0))
+        return fail(ctx, SUNB_ILL_INPUT, "graph: need y, 1 <= nsteps <= 4096, dt > 0, finite t0");
+    if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
+    if (ctx->d_tape) return fail(ctx, SUNB_ILL_INPUT, "graph: adjoint-recording contexts integrate one step per call");
+    if (ctx->autotune && !ctx->tuned && ctx->tune_cells > 0 && (ctx->kind == SUNB_MECHANISM || ctx->kind == SUNB_MIXED)) {
+        const int rc = autotune(ctx, dev_y, t0, t0 + dt);    // the trials synchronise: before building
+        if (rc != SUNB_SUCCESS) return rc;
+    }
+    if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
+    if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
+    ctx->graph_kernels.assign(nsteps, nullptr);
+    ctx->graph_margs.assign(nsteps, MechArgs{});
+    ctx->graph_targs.assign(nsteps, ThreadArgs{});
+    CU(cudaGraphCreate(&ctx->graph, 0));
+    cudaGraphNode_t prev = nullptr;
+    for (int k = 0; k < nsteps; ++k) {
+        const double a = t0 + k * dt, b = t0 + (k + 1) * dt;
+        int rc = step_config(ctx, dev_y, a, b, dev_status, &ctx->graph_func, ctx->graph_grid, ctx->graph_block,
+                             ctx->graph_smem, ctx->graph_margs[k], ctx->graph_targs[k]);
+        if (rc != SUNB_SUCCESS) return rc;
+        cudaMemsetParams mp{};
+        mp.dst = ctx->d_queue;
+        mp.value = 0;
+        mp.elementSize = 4;
+        mp.width = 4;
+        mp.height = 1;
+        mp.pitch = 0;
+        cudaGraphNode_t mnode;
+        CU(cudaGraphAddMemsetNode(&mnode, ctx->graph, prev ? &prev : nullptr, prev ? 1 : 0, &mp));
+        cudaKernelNodeParams kp{};
+        kp.func = ctx->graph_func;
+        kp.gridDim = ctx->graph_grid;
+        kp.blockDim = ctx->graph_block;
+        kp.sharedMemBytes = ctx->graph_smem;
+        void *argp = (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)
+                         ? (void *)&ctx->graph_targs[k] : (void *)&ctx->graph_margs[k];
+        void *args[] = {argp};
+        kp.kernelParams = args;
+        CU(cudaGraphAddKernelNode(&ctx->graph_kernels[k], ctx->graph, &mnode, 1, &kp));
+        prev = ctx->graph_kernels[k];
+    }
+    CU(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
+    ctx->graph_dt = dt;
+    return SUNB_SUCCESS;
+}
+
+int sunb_graph_launch(sunb_ctx *ctx, double t0)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!ctx->graph_exec) return fail(ctx, SUNB_ILL_INPUT, "no captured graph (sunb_graph_capture)");
+    if (!std::isfinite(t0)) return fail(ctx, SUNB_ILL_INPUT, "t0 must be finite");
+    const bool thread = ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY;
+    for (size_t k = 0; k < ctx->graph_kernels.size(); ++k) {
+        Controls &c = thread ? ctx->graph_targs[k].ctl : ctx->graph_margs[k].ctl;
+        c.t0 = t0 + (double)k * ctx->graph_dt;
+        c.tout = t0 + (double)(k + 1) * ctx->graph_dt;
+        cudaKernelNodeParams kp{};
+        kp.func = ctx->graph_func;
+        kp.gridDim = ctx->graph_grid;
+        kp.blockDim = ctx->graph_block;
+        kp.sharedMemBytes = ctx->graph_smem;
+        void *argp = thread ? (void *)&ctx->graph_targs[k] : (void *)&ctx->graph_margs[k];
+        void *args[] = {argp};
+        kp.kernelParams = args;
+        CU(cudaGraphExecKernelNodeSetParams(ctx->graph_exec, ctx->graph_kernels[k], &kp));
+    }
+    CU(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
+    ctx->launches += (int64_t)ctx->graph_kernels.size();
     return SUNB_SUCCESS;
 }
 
