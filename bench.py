@@ -59,22 +59,37 @@ def jac_extra_flops(mech):
     return M * 22 + nnz * 14 + 2 * K * K + 2 * K * K + 4 * K * K + 10 * K + N * N
 
 
-def work_model(w, tot):
+def work_model(kind, mech, tot):
     """Algorithmic FP64 flops of one launch from the per-cell counters:
     f evaluations, Newton-matrix builds (J + LU (2/3)N^3), Newton iterations
     (solve 2N^2 + 8N vector work) and steps (predict, correct, weights,
-    norms; order 4 taken as typical)."""
-    if w["kind"] == "mechanism":
-        N = w["mech"].n_vars
-        f_rhs = rhs_flops(w["mech"])
-        f_setup = jac_extra_flops(w["mech"]) + (2.0 / 3.0) * N ** 3
-    else:
+    norms; order 4 taken as typical).  An exponential or logarithm counts as
+    one operation."""
+    if kind == "mechanism":
+        N = mech.n_vars
+        f_rhs = rhs_flops(mech)
+        f_setup = jac_extra_flops(mech) + (2.0 / 3.0) * N ** 3
+    elif kind == "robertson":
         N = 3
         f_rhs, f_setup = 12, 9 + (2.0 / 3.0) * 27
+    else:   # cosmology: log, 6 compares, 2 exponentials, power-law algebra
+        N = 1
+        f_rhs, f_setup = 20, 8
     q = 4
     f_step = (q * (q + 1) / 2) * N + 2 * (q + 1) * N + 3 * N + 8 * N + 120
     f_iter = 2 * N * N + 8 * N
     return (tot["nfe"] * f_rhs + tot["nje"] * f_setup + tot["nni"] * f_iter + tot["nst"] * f_step)
+
+
+def split_totals(cs, n_first):
+    """Counter sums of cells [0, n_first) and [n_first, C) of a device
+    [C, 8] statistics tensor."""
+    out = []
+    for part in (cs[:n_first], cs[n_first:]):
+        s = part[:, :6].sum(dim=0, dtype=__import__("torch").int64).cpu().numpy()
+        out.append(dict(nst=int(s[0]), nfe=int(s[1]), nje=int(s[2]), nni=int(s[3]),
+                        ncf=int(s[4]), nef=int(s[5])))
+    return out
 
 
 # --------------------------------------------------------------------- clocks
@@ -148,6 +163,8 @@ def make_workload(name, cells=None):
             synth.workloads.mixed(n_cosmo=cells * 256, n_mech=cells)
     if name == "cosmology":
         return synth.workloads.cosmology(2 ** 24 if cells is None else cells)
+    if name == "adjoint":
+        return synth.workloads.adjoint(**kw)
     raise ValueError(name)
 
 
@@ -178,21 +195,46 @@ def make_integrator(w, form):
                             schedule=kw["schedule"])
 
 
+ADJOINT_CAP = 1536   # tape capacity (accepted steps per cell) of the adjoint workload
+
+
 def time_form(w, form, steps, warmup, flush):
     """Device-resident timing of one form: per step, copy y0 -> y and
-    integrate, bracketed by CUDA events on the integrator's stream; an L2
-    flush (a 512 MiB write) runs between steps outside the events."""
+    integrate (for the adjoint workload: integrate with tapes, replay, and
+    the reverse sweep to the [M, 2] gradient of the squared-error loss),
+    bracketed by CUDA events on the integrator's stream; an L2 flush (a
+    512 MiB write) runs between steps outside the events."""
     import torch
     Y, P, C = flat_inputs(w)
-    it = make_integrator(w, form)
+    adjoint = w["name"] == "adjoint"
+    if adjoint:
+        import paper_2405_01713_b300 as sb
+        kw = FORMS[form]
+        it = sb.Integrator(sb.MECHANISM, w["n_cells"], mech=w["mech"], record_adjoint=ADJOINT_CAP,
+                           precision=kw["precision"], lanes_per_cell=kw["lanes_per_cell"],
+                           schedule=kw["schedule"])
+        it.set_tolerances(w["rtol"], w["atol"])
+        K = w["mech"].n_species
+        target = torch.tensor(w["target"], device="cuda")
+        dL = torch.zeros((C, w["mech"].n_vars), dtype=torch.float64, device="cuda")
+        yrep = torch.empty_like(dL)
+    else:
+        it = make_integrator(w, form)
     stream = torch.cuda.current_stream()
     y0 = torch.tensor(Y, device="cuda")
     y = torch.empty_like(y0)
     p = torch.tensor(P, device="cuda")
     it.set_params(p)
-    for _ in range(warmup):
+    def one_step():
         y.copy_(y0)
         it.integrate(y, w["t0"], w["tout"])
+        if adjoint:
+            it.adjoint_replay(yrep)
+            dL[:, :K] = 2 * (yrep[:, :K] - target)
+            it.adjoint(dL)
+
+    for _ in range(warmup):
+        one_step()
     torch.cuda.synchronize()
     l0 = it.launch_count
     times = []
@@ -201,16 +243,18 @@ def time_form(w, form, steps, warmup, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        y.copy_(y0)
-        it.integrate(y, w["t0"], w["tout"])
+        one_step()
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
     launches = it.launch_count - l0
     tot = it.totals()
+    parts = None
+    if w["kind"] == "mixed":
+        parts = split_totals(it.cell_stats(), w["n_cosmo"])
     mapping = it.mapping() if w["kind"] in ("mechanism", "mixed") else None
     it.close()
-    return dict(ms=times, launches=launches, totals=tot, mapping=mapping, C=C)
+    return dict(ms=times, launches=launches, totals=tot, mapping=mapping, C=C, parts=parts)
 
 
 def time_e2e(w, form, steps, warmup):
@@ -241,25 +285,30 @@ def time_e2e(w, form, steps, warmup):
 # --------------------------------------------------------------------- CPU baseline
 def cpu_baseline(w, budget_s=12.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
-    the workload (the first n cells; n sized to ~budget_s)."""
+    the workload (the first n cells; n grown until the sample takes a
+    fraction of budget_s), extrapolated to the full batch.  For the adjoint
+    workload the oracle runs its forward, replay and adjoint."""
     import oracle
     nth = oracle.num_threads()
     if w["kind"] == "mixed":
-        wc = synth.workloads.cosmology(4096)
         wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
                   t0=0.0, tout=w["tout"])
-        parts = [(wc, w["n_cosmo"]), (wm, w["n_mech"])]
+        parts = [("cosmology", w["n_cosmo"]), (wm, w["n_mech"])]
     else:
         parts = [(w, w["n_cells"])]
     total_s, descr = 0.0, []
     for ww, Cfull in parts:
         n = min(Cfull, 2 * nth)
         while True:
-            cells = np.arange(n)
-            pb = oracle.problem_from_workload(ww, cells=cells)
+            sample = synth.workloads.cosmology(n) if ww == "cosmology" else ww
+            pb = oracle.problem_from_workload(sample, cells=np.arange(n))
             t = time.perf_counter()
-            oracle.integrate(pb, ww["y0"][:n], ww["t0"], ww["tout"], ww.get("rtol", 1e-6),
-                             ww.get("atol", 1e-10), nthreads=nth)
+            if w.get("name") == "adjoint":
+                oracle.adjoint_sqerr(pb, sample["y0"][:n], sample["target"][:n], sample["t0"],
+                                     sample["tout"], 1e-6, 1e-10, cap=4096, nthreads=nth)
+            else:
+                oracle.integrate(pb, sample["y0"][:n], sample["t0"], sample["tout"], 1e-6, 1e-10,
+                                 nthreads=nth)
             dt = time.perf_counter() - t
             if dt > budget_s / len(parts) / 4 or n >= Cfull:
                 break
@@ -278,7 +327,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="sunb", choices=["sunb", "reference"])
     ap.add_argument("--workload", default="mech22",
-                    choices=["mech22", "mech54", "mixed", "robertson", "cosmology"])
+                    choices=["mech22", "mech54", "mixed", "robertson", "cosmology", "adjoint"])
     ap.add_argument("--no-plain", action="store_true", help="skip the plain-form comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     ap.add_argument("--no-e2e", action="store_true")
@@ -292,11 +341,14 @@ def main():
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     w = make_workload(args.workload, args.cells)
+    w.setdefault("name", args.workload)
     workload_name = {"mech22": "mech22: 21 species + T, 84 reactions, 2^18 cells, dt 1e-6 s",
                      "mech54": "mech54: 53 species + T, 270 reactions, 2^20 cells, dt 1e-6 s",
                      "mixed": "mixed: 2^24 cosmology cells + 2^16 mech22 cells, dt 1e-6 s",
                      "robertson": "robertson: 1024 cells, t 0 -> 1e5",
-                     "cosmology": "cosmology: 2^24 cells, dt 1e-6 s"}[args.workload]
+                     "cosmology": "cosmology: 2^24 cells, dt 1e-6 s",
+                     "adjoint": "adjoint: mech22 mechanism, 2^16 cells, dt 1e-5 s, gradient of the "
+                                "squared-error loss w.r.t. 84x2 (ln A, Ea)"}[args.workload]
     if args.cells is not None:
         workload_name += f" (first {args.cells} cells only)"
 
@@ -304,9 +356,10 @@ def main():
         if rank != 0:
             return
         cb = cpu_baseline(w, budget_s=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
+        C = w["n_cosmo"] + w["n_mech"] if w["kind"] == "mixed" else w["n_cells"]
         line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": None, "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": 1e3 * C / cb["value"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
                 "config": {"workload": workload_name, "rtol": 1e-6, "atol": 1e-10},
                 "cpu_baseline": cb,
@@ -324,7 +377,7 @@ def main():
 
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     res_plain = None
-    if not args.no_plain and w["kind"] in ("mechanism", "mixed"):
+    if not args.no_plain and w["kind"] in ("mechanism", "mixed") and w["name"] != "adjoint":
         res_plain = time_form(w, "plain", args.steps, args.warmup, flush)
     clocks.start()
     res = time_form(w, "chosen", args.steps, args.warmup, flush)
@@ -338,8 +391,18 @@ def main():
     value = world * res["C"] / (ms / 1e3)
 
     # the counters describe the last launch (they are reset by every call)
-    flops = work_model(w if w["kind"] != "mixed" else dict(kind="mechanism", mech=w["mech"]),
-                       res["totals"])
+    if w["kind"] == "mixed":
+        flops = work_model("cosmology", None, res["parts"][0]) + \
+            work_model("mechanism", w["mech"], res["parts"][1])
+    elif w["name"] == "adjoint":
+        # forward + replay (taken as 2 exact Newton iterations per step) +
+        # reverse sweep (one J, LU and transposed solve per step)
+        mech, t = w["mech"], res["totals"]
+        N = mech.n_vars
+        per_setup = rhs_flops(mech) + jac_extra_flops(mech) + (2.0 / 3.0) * N ** 3 + 2 * N * N
+        flops = work_model("mechanism", mech, t) + t["nst"] * (3 * per_setup + 12 * mech.n_reactions)
+    else:
+        flops = work_model(w["kind"], w.get("mech"), res["totals"])
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
             "frac": achieved / FP64_PEAK_DERIVED, "traffic": None,
@@ -364,7 +427,9 @@ def main():
                          "chosen": {"value": res["C"] / (ms / 1e3), "ms_per_step": ms,
                                     "mapping": res["mapping"][:3],
                                     "autotune_trial_ms": res["mapping"][3]}}
-    if not args.no_e2e:
+    if res["parts"] is not None:
+        line["work_by_kind"] = {"cosmology": res["parts"][0], "mechanism": res["parts"][1]}
+    if not args.no_e2e and w["name"] != "adjoint":
         line["e2e"] = time_e2e(w, "chosen", max(1, min(args.steps, 2)), 1)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
