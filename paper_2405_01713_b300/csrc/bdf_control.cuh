@@ -121,72 +121,130 @@ __device__ __forceinline__ double eta_viable2(int p)
     return r;
 }
 
+// The controller as a state machine that advances a cell by at most one
+// Newton iteration per call ("superstep").  Its phases -- STEP (start a
+// step), ATTEMPT (predict, coefficients), SETUP (f and the Newton matrix at
+// the prediction), NEWTON (one iteration: f, solve, convergence test) and
+// POST (Newton failure, error test, accept, step and order selection) --
+// are visited in this fixed order inside a superstep.  Cells that share a
+// warp (a thread per cell, or several lane groups per warp) therefore reach
+// the one right-hand-side call of NEWTON and the one set-up call of SETUP
+// together, whatever their step counts, instead of diverging through
+// nested loops.  A cell's arithmetic is exactly that of the sequential
+// algorithm (bdf_cell below runs it sequentially).
+enum Phase : int {
+    PH_STEP = 0, PH_ATTEMPT = 1, PH_SETUP = 2, PH_NEWTON = 3, PH_POST = 4,
+    PH_DONE = 5,    // finished; the caller collects s and may begin another cell
+    PH_EXIT = 6     // no cell left for this thread or group (set by run_cells)
+};
+
 template <class C>
-__device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
-{
-    const double t0 = ctl.t0, tout = ctl.tout;
-    const int qmax = ctl.max_order < 1 ? 1 : (ctl.max_order > QMAX ? QMAX : ctl.max_order);
-    s.nst = s.nfe = s.nje = s.nni = s.ncf = s.nef = 0;
-    s.qlast = 1;
-    s.status = ST_SUCCESS;
-
-    c.load_y(V_Z0);
-    if (!(tout > t0)) { c.store_y(V_Z0); return; }
-    c.rhs(V_Z0, V_F);
-    s.nfe++;
-    if (!c.all_finite(V_F) || !c.all_finite(V_Z0)) {
-        s.status = ST_NONFINITE;
-        c.store_y(V_Z0);
-        return;
-    }
-    c.set_weights(V_Z0, ctl.rtol);
-
-    // ---- starting step (Hairer, Norsett & Wanner, order 1) ----
-    double h;
-    {
-        const double span = tout - t0;
-        const double d0 = c.wrms2(V_Z0), d1 = c.wrms2(V_F);   // squared
-        double h0 = (d0 < 1e-10 || d1 < 1e-10) ? 1e-6 * span : 0.01 * sqrt(d0 * rcp(d1));
-        if (h0 > span) h0 = span;
-        c.axpby(V_Y, 1.0, V_Z0, h0, V_F);
-        c.rhs(V_Y, V_DEL);
-        s.nfe++;
-        const double rh0 = rcp(h0);
-        const double d2 = c.wrms2_lin(rh0, V_DEL, -rh0, V_F);
-        const double dm = fmax(d1, d2);
-        double h1 = (dm <= 1e-30) ? fmax(1e-6 * span, h0 * 1e-3) : sqrt(0.01 * rcp(sqrt(dm)));
-        h = fmin(100.0 * h0, h1);
-        if (!(h > 0.0)) h = 1e-6 * span;
-        h = fmin(h, span);
-    }
-    c.scale(V_Z1, h, V_F);
-    c.rec_init(h);
-
-    double t = t0;
-    int q = 1, qwait = 2, have_M = 0, force_setup = 1, nst_lastsetup = 0, have_ks = 0;
+struct CellRun {
+    int phase;
+    CellStats s;
+    int qmax;
+    // integration state
+    double tout, t, h, gamma_M, etamax, h_ks;
     double hist[QMAX + 1];
-#pragma unroll
-    for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
-    double gamma_M = 0.0, etamax = ETA_MAX_FIRST, h_ks = 0.0;
-    int nsame = 0;    // leading entries of hist equal to the current h
+    int q, qwait, have_M, force_setup, nst_lastsetup, have_ks, nsame;
+    // current step / attempt
+    int last, ncf, nef;
+    double dsm2, Cq, il1, gamma;
+    double l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1];
+    // current Newton solve
+    int fresh, conv, fcur, m;
+    double delp2, R2, cstale;
 
-    while (t < tout) {
-        if (s.nst >= ctl.max_steps) { s.status = ST_TOO_MUCH_WORK; break; }
-        int last = 0;
-        if (t + h >= tout || tout - (t + h) <= 4.0 * 2.220446049250313e-16 * fabs(tout)) {
-            const double hn = tout - t;
-            c.rescale(q, hn * rcp(h));
-            h = hn;
-            last = 1;
-            nsame = 0;
+    __device__ void finish(C &c)
+    {
+        s.qlast = q;
+        c.store_y(V_Z0);
+        phase = PH_DONE;
+    }
+
+    // first steps of a cell: load, f(t0, y0), weights, starting step size
+    __device__ void begin(C &c, const Controls &ctl)
+    {
+        const double t0 = ctl.t0;
+        tout = ctl.tout;
+        qmax = ctl.max_order < 1 ? 1 : (ctl.max_order > QMAX ? QMAX : ctl.max_order);
+        s.nst = s.nfe = s.nje = s.nni = s.ncf = s.nef = 0;
+        s.qlast = 1;
+        s.status = ST_SUCCESS;
+        q = 1;
+        c.load_y(V_Z0);
+        if (!(tout > t0)) { finish(c); return; }
+        c.rhs(V_Z0, V_F);
+        s.nfe++;
+        if (!c.all_finite(V_F) || !c.all_finite(V_Z0)) {
+            s.status = ST_NONFINITE;
+            finish(c);
+            return;
         }
-        c.set_weights(V_Z0, ctl.rtol);          // Eq. wrms: weights from y^{n-1}
-        int ncf = 0, nef = 0;
-        double dsm2 = 0.0, l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1], Cq = 0.0;
-        double gamma_acc = 0.0, il1_acc = 0.0;     // of the attempt that is accepted
-        for (;;) {   // attempts
+        c.set_weights(V_Z0, ctl.rtol);
+        // starting step (Hairer, Norsett & Wanner, order 1)
+        {
+            const double span = tout - t0;
+            const double d0 = c.wrms2(V_Z0), d1 = c.wrms2(V_F);   // squared
+            double h0 = (d0 < 1e-10 || d1 < 1e-10) ? 1e-6 * span : 0.01 * sqrt(d0 * rcp(d1));
+            if (h0 > span) h0 = span;
+            c.axpby(V_Y, 1.0, V_Z0, h0, V_F);
+            c.rhs(V_Y, V_DEL);
+            s.nfe++;
+            const double rh0 = rcp(h0);
+            const double d2 = c.wrms2_lin(rh0, V_DEL, -rh0, V_F);
+            const double dm = fmax(d1, d2);
+            double h1 = (dm <= 1e-30) ? fmax(1e-6 * span, h0 * 1e-3) : sqrt(0.01 * rcp(sqrt(dm)));
+            h = fmin(100.0 * h0, h1);
+            if (!(h > 0.0)) h = 1e-6 * span;
+            h = fmin(h, span);
+        }
+        c.scale(V_Z1, h, V_F);
+        c.rec_init(h);
+        t = t0;
+        qwait = 2; have_M = 0; force_setup = 1; nst_lastsetup = 0; have_ks = 0; nsame = 0;
+#pragma unroll
+        for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
+        gamma_M = 0.0; etamax = ETA_MAX_FIRST; h_ks = 0.0;
+        phase = PH_STEP;
+    }
+
+    __device__ void start_newton(C &c)
+    {
+        if (!have_M) { conv = 0; phase = PH_POST; return; }
+        c.newton_init();
+        delp2 = 0.0;
+        R2 = 1.0;
+        cstale = (gamma != gamma_M) ? 2.0 * rcp(1.0 + gamma * rcp(gamma_M)) : 1.0;
+        m = 0;
+        phase = PH_NEWTON;
+    }
+
+    __device__ void superstep(C &c, const Controls &ctl)
+    {
+        if (phase == PH_STEP) {
+            if (!(t < tout)) {
+                finish(c);
+            } else if (s.nst >= ctl.max_steps) {
+                s.status = ST_TOO_MUCH_WORK;
+                finish(c);
+            } else {
+                last = 0;
+                if (t + h >= tout || tout - (t + h) <= 4.0 * 2.220446049250313e-16 * fabs(tout)) {
+                    const double hn = tout - t;
+                    c.rescale(q, hn * rcp(h));
+                    h = hn;
+                    last = 1;
+                    nsame = 0;
+                }
+                c.set_weights(V_Z0, ctl.rtol);          // Eq. wrms: weights from y^{n-1}
+                ncf = 0;
+                nef = 0;
+                phase = PH_ATTEMPT;
+            }
+        }
+        if (phase == PH_ATTEMPT) {
             c.predict(q);
-            double il1;
             if (nsame >= q) {
 #pragma unroll
                 for (int i = 0; i <= QMAX; ++i) {
@@ -202,57 +260,67 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 il1 = rcp(l[1]);
                 Cq = rcp(1.0 + l[1] * xi[q]);
             }
-            const double gamma = h * il1;
-            gamma_acc = gamma;
-            il1_acc = il1;
-            const double Cq2 = Cq * Cq;
-            int fresh = 0, conv = 0, fcur = 0;   // fcur: V_F holds f(z0) already
+            gamma = h * il1;
+            fresh = 0;
+            fcur = 0;
             if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
-                fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX) {
-                have_M = c.rhs_setup(V_Z0, V_F, gamma);
-                s.nje++; s.nfe++;
-                gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; force_setup = 0; fcur = 1;
+                fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX)
+                phase = PH_SETUP;
+            else
+                start_newton(c);
+        }
+        if (phase == PH_SETUP) {
+            have_M = c.rhs_setup(V_Z0, V_F, gamma);
+            s.nje++;
+            s.nfe++;
+            gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; force_setup = 0;
+            fcur = 1;                                        // V_F holds f(z0)
+            start_newton(c);
+        }
+        if (phase == PH_NEWTON) {     // one modified-Newton iteration (Eq. stop_newton)
+            if (!fcur) { c.rhs(V_Y, V_F); s.nfe++; }
+            fcur = 0;
+            s.nni++;
+            c.newton_residual(h, il1);
+            c.solve(V_DEL);
+            const double dn2 = c.newton_update(cstale);
+            bool done = false;
+            conv = 0;
+            if (!(dn2 <= 1.7e308)) {
+                done = true;                                 // not finite
+            } else {
+                if (m > 0) R2 = fmax(CRDOWN * CRDOWN * R2, dn2 * rcp(delp2));
+                if (R2 * dn2 * (Cq * Cq) < NLS_COEF * NLS_COEF) { conv = 1; done = true; }
+                else if (m + 1 == MAXCOR || (m > 0 && dn2 > RDIV * RDIV * delp2)) done = true;
+                else { delp2 = dn2; ++m; }
             }
-            for (;;) {   // Newton
-                conv = 0;
-                if (!have_M) break;
-                c.newton_init();
-                double delp2 = 0.0, R2 = 1.0;
-                const double cstale = (gamma != gamma_M) ? 2.0 * rcp(1.0 + gamma * rcp(gamma_M)) : 1.0;
-                for (int m = 0;; ++m) {
-                    if (!fcur) { c.rhs(V_Y, V_F); s.nfe++; }
-                    fcur = 0;
-                    s.nni++;
-                    c.newton_residual(h, il1);
-                    c.solve(V_DEL);
-                    const double dn2 = c.newton_update(cstale);
-                    if (!(dn2 <= 1.7e308)) break;             // not finite
-                    if (m > 0) R2 = fmax(CRDOWN * CRDOWN * R2, dn2 * rcp(delp2));
-                    if (R2 * dn2 * Cq2 < NLS_COEF * NLS_COEF) { conv = 1; break; }
-                    if (m + 1 == MAXCOR || (m > 0 && dn2 > RDIV * RDIV * delp2)) break;
-                    delp2 = dn2;
-                }
-                if (conv || fresh) break;
-                have_M = c.rhs_setup(V_Z0, V_F, gamma);    // stale matrix: rebuild and retry
-                s.nje++; s.nfe++;
-                gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; fcur = 1;
-            }
-            if (!conv) {   // Newton failure
-                c.unpredict(q);
-                s.ncf++; ncf++;
-                if (ncf >= MXNCF) { s.status = ST_CONV_FAILURE; break; }
-                h *= ETA_CF;
-                c.rescale(q, ETA_CF);
-                force_setup = 1; etamax = 1.0; last = 0; nsame = 0;
-                if (t + h == t) { s.status = ST_H_TOO_SMALL; break; }
-                continue;
-            }
-            dsm2 = Cq2 * c.wrms2(V_ACOR);
-            if (dsm2 < 1.0) break;     // accept: ||LTE|| < 1
-            // error-test failure
+            if (done) phase = PH_POST;
+        }
+        if (phase == PH_POST) post(c);
+    }
+
+    __device__ void post(C &c)
+    {
+        if (!conv && !fresh) {        // stale matrix: rebuild at the predicted state and retry
+            phase = PH_SETUP;
+            return;
+        }
+        if (!conv) {                  // Newton failure
+            c.unpredict(q);
+            s.ncf++; ncf++;
+            if (ncf >= MXNCF) { s.status = ST_CONV_FAILURE; finish(c); return; }
+            h *= ETA_CF;
+            c.rescale(q, ETA_CF);
+            force_setup = 1; etamax = 1.0; last = 0; nsame = 0;
+            if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
+            phase = PH_ATTEMPT;
+            return;
+        }
+        dsm2 = (Cq * Cq) * c.wrms2(V_ACOR);
+        if (dsm2 >= 1.0) {            // error-test failure (accept iff ||LTE|| < 1)
             c.unpredict(q);
             s.nef++; nef++;
-            if (nef >= MXNEF) { s.status = ST_ERR_FAILURE; break; }
+            if (nef >= MXNEF) { s.status = ST_ERR_FAILURE; finish(c); return; }
             if (nef < MXNEF1) {
                 double eta = eta_from(dsm2, q, BIAS_Q);
                 int newq = q;
@@ -298,9 +366,10 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
                 qwait = 2; have_ks = 0;
             }
             etamax = 1.0; last = 0; nsame = 0;
-            if (t + h == t) { s.status = ST_H_TOO_SMALL; break; }
+            if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
+            phase = PH_ATTEMPT;
+            return;
         }
-        if (s.status != ST_SUCCESS) break;
 
         // ---- accepted step ----
         s.nst++;
@@ -310,10 +379,10 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
         hist[0] = h;
         if (last) {
-            c.rec_accept(q, q, l, 0.0, gamma_acc, il1_acc);
-            break;
+            c.rec_accept(q, q, l, 0.0, gamma, il1);
+            finish(c);
+            return;
         }
-
         qwait--;
         const double l1 = l[1];
         double eta = 1.0;
@@ -345,7 +414,7 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
         }
         if (eta < ETA_THRESH) { eta = 1.0; newq = q; }
         else eta = fmin(eta, etamax);
-        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma_acc, il1_acc);
+        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma, il1);
         if (newq == q + 1) c.order_increase(q, l, inv[q]);
         else if (newq == q - 1) {
             double e[QMAX + 1];
@@ -365,9 +434,55 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
             ++nsame;
         }
         etamax = ETA_MAX;
+        phase = PH_STEP;
     }
-    s.qlast = q;
-    c.store_y(V_Z0);
+};
+
+// One cell from start to finish (the sequential use of the state machine).
+template <class C>
+__device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
+{
+    CellRun<C> run;
+    run.begin(c, ctl);
+    while (run.phase != PH_DONE) run.superstep(c, ctl);
+    s = run.s;
+}
+
+// Runs the cells handed out by next() (a cell index, or -1 when none is
+// left) on this thread or lane group, one superstep at a time: a thread
+// (group) whose cell finishes begins its next cell at once while the rest
+// of its warp keeps stepping.  wmask holds the warp's launched threads; the
+// loop ends when none of them has a cell left.  bind(cell) points the
+// backend at a cell before it begins; done(cell, stats) reports it.
+template <class C, class Next, class Bind, class Done>
+__device__ __forceinline__ void run_cells(C &c, const Controls &ctl, unsigned wmask, Next next,
+                                          Bind bind, Done done)
+{
+    CellRun<C> run;
+    run.phase = PH_DONE;
+    long long cell = -1;
+    for (;;) {
+        if (run.phase == PH_DONE) {
+            cell = next();
+            if (cell >= 0) {
+                bind(cell);
+                run.begin(c, ctl);
+            } else {
+                run.phase = PH_EXIT;
+            }
+        }
+        if (__all_sync(wmask, run.phase == PH_EXIT)) break;
+        if (run.phase < PH_DONE) run.superstep(c, ctl);
+        if (run.phase == PH_DONE) done(cell, run.s);
+    }
+}
+
+// Mask of the launched threads of the calling thread's warp.
+__device__ __forceinline__ unsigned launched_warp_mask()
+{
+    const int first = (int)(threadIdx.x & ~31u);
+    const int n = min(32, (int)blockDim.x - first);
+    return n >= 32 ? 0xffffffffu : ((1u << n) - 1u);
 }
 
 }  // namespace sunb

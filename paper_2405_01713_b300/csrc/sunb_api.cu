@@ -116,8 +116,11 @@ __device__ __forceinline__ unsigned group_mask()
 }
 
 // Persistent mechanism kernel: L lanes per cell, cells_per_cta cells per
-// CTA, one CTA set per SM; the cosmology cells of a mixed launch are taken
-// one per thread after the mechanism queue runs dry (the larger cells first).
+// CTA, one CTA set per SM.  In a mixed launch the mechanism cells (the
+// larger ones) go first; threads whose group finds the mechanism queue
+// empty fill the kernel's tail with cosmology cells, one per thread.
+// Counters: queue[0] mechanism cells handed out, queue[1] cosmology cells
+// handed out, queue[2] mechanism cells finished (mixed launches).
 template <int L, typename MT, bool COSMO>
 __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
 {
@@ -136,36 +139,55 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
     c.invN = a.invN;
     c.bind(smem + a.off.bytes + gid * a.lay.bytes, a.lay);
 
+    const unsigned wmask = launched_warp_mask();
     long long next = (long long)blockIdx.x * a.cells_per_cta + gid;
     const long long stride = (long long)gridDim.x * a.cells_per_cta;
-    for (;;) {
-        long long cell;
-        if (a.schedule == SUNB_SCHED_QUEUE) cell = grab_group(a.queue, c.g.lane, c.g.mask, L);
-        else { cell = next; next += stride; }
-        if (cell >= a.n_mech) break;
-        c.P = a.p_mech[cell];
-        c.invP = rcp(c.P);
-        c.yg = a.y_mech + cell * c.N;
-        c.tape = a.tape ? a.tape + cell * a.tape_stride : nullptr;
-        c.tape_cap = a.tape_cap;
-        CellStats st;
-        bdf_cell(c, a.ctl, st);
-        if (c.g.lane == 0) write_stats(a.stats_mech, a.status_mech, cell, st);
-    }
+    run_cells(
+        c, a.ctl, wmask,
+        [&]() -> long long {
+            long long cell;
+            if (a.schedule == SUNB_SCHED_QUEUE) cell = grab_group(a.queue, c.g.lane, c.g.mask, L);
+            else { cell = next; next += stride; }
+            return cell < a.n_mech ? cell : -1;
+        },
+        [&](long long cell) {
+            c.P = a.p_mech[cell];
+            c.invP = rcp(c.P);
+            c.yg = a.y_mech + cell * c.N;
+            c.tape = a.tape ? a.tape + cell * a.tape_stride : nullptr;
+            c.tape_cap = a.tape_cap;
+        },
+        [&](long long cell, const CellStats &st) {
+            if (c.g.lane == 0) {
+                write_stats(a.stats_mech, a.status_mech, cell, st);
+                if (COSMO) atomicAdd(a.queue + 2, 1ull);
+            }
+        });
     if (COSMO) {
-        __syncwarp();
-        for (;;) {
-            const long long cell = grab_thread(a.queue + 1);
-            if (cell >= a.n_cosmo) break;
-            ThreadCell<CosmologyProblem> tc;
-            tc.prob.tab = &cool;
-            tc.prob.load(a.p_cosmo, cell);
-            tc.atol[0] = a.atol_cosmo;
-            tc.yg = a.y_cosmo + cell;
-            CellStats st;
-            bdf_cell(tc, a.ctl, st);
-            write_stats(a.stats_cosmo, a.status_cosmo, cell, st);
-        }
+        // While other groups still integrate mechanism cells, idle threads
+        // take cosmology cells (one per thread) from the shared counter;
+        // once every mechanism cell is done they stop, and the cosmology
+        // kernel that follows on the stream runs the rest at full occupancy.
+        __syncwarp(wmask);
+        ThreadCell<CosmologyProblem> tc;
+        tc.prob.tab = &cool;
+        tc.atol[0] = a.atol_cosmo;
+        run_cells(
+            tc, a.ctl, wmask,
+            [&]() -> long long {
+                if (*reinterpret_cast<volatile unsigned long long *>(a.queue + 2) >=
+                    (unsigned long long)a.n_mech)
+                    return -1;
+                const long long cell = grab_thread(a.queue + 1);
+                return cell < a.n_cosmo ? cell : -1;
+            },
+            [&](long long cell) {
+                tc.prob.load(a.p_cosmo, cell);
+                tc.yg = a.y_cosmo + cell;
+            },
+            [&](long long cell, const CellStats &st) {
+                write_stats(a.stats_cosmo, a.status_cosmo, cell, st);
+            });
     }
 }
 
@@ -188,19 +210,21 @@ __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();
-    for (;;) {
-        const long long cell = grab_thread(a.queue);
-        if (cell >= a.n) break;
-        ThreadCell<Prob> tc;
-        if constexpr (Prob::N == 1) tc.prob.tab = &cool;
-        tc.prob.load(a.params, cell);
+    ThreadCell<Prob> tc;
+    if constexpr (Prob::N == 1) tc.prob.tab = &cool;
 #pragma unroll
-        for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
-        tc.yg = a.y + cell * Prob::N;
-        CellStats st;
-        bdf_cell(tc, a.ctl, st);
-        write_stats(a.stats, a.status, cell, st);
-    }
+    for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
+    run_cells(
+        tc, a.ctl, launched_warp_mask(),
+        [&]() -> long long {
+            const long long cell = grab_thread(a.queue);
+            return cell < a.n ? cell : -1;
+        },
+        [&](long long cell) {
+            tc.prob.load(a.params, cell);
+            tc.yg = a.y + cell * Prob::N;
+        },
+        [&](long long cell, const CellStats &st) { write_stats(a.stats, a.status, cell, st); });
 }
 
 // Batched right-hand side (mode 0) or Jacobian (mode 1) of a mechanism:
@@ -557,6 +581,17 @@ __global__ void totals_kernel(const int32_t *stats, long long n, DevTotals *t)
 
 // ============================================================ host side
 
+// One kernel launch of an outer step.
+struct LaunchSpec {
+    void *func = nullptr;
+    dim3 grid, block;
+    int smem = 0;
+    bool thread = false;    // arguments in ta (thread kernel) or ma (mechanism kernel)
+    MechArgs ma{};
+    ThreadArgs ta{};
+    void *arg() { return thread ? (void *)&ta : (void *)&ma; }
+};
+
 struct sunb_ctx {
     int kind = 0;
     long long C = 0, Cc = 0;         // mechanism (or Robertson/cosmology) cells, cosmology cells (mixed)
@@ -593,12 +628,9 @@ struct sunb_ctx {
     // CUDA graph of captured outer steps
     cudaGraph_t graph = nullptr;
     cudaGraphExec_t graph_exec = nullptr;
-    std::vector<cudaGraphNode_t> graph_kernels;
-    std::vector<MechArgs> graph_margs;
-    std::vector<ThreadArgs> graph_targs;
-    void *graph_func = nullptr;
-    dim3 graph_grid, graph_block;
-    int graph_smem = 0;
+    std::vector<cudaGraphNode_t> graph_kernels;    // kernel nodes, step-major
+    std::vector<LaunchSpec> graph_specs;          // their launches, same order
+    std::vector<int> graph_step;                  // the outer step of each node
     double graph_dt = 0.0;
     double *d_gpart = nullptr;       // partial sums of the gradient reduction
     long long tune_cells = 0;
@@ -849,7 +881,7 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
     const int bytes = fixed + ctx->cells_per_cta * ctx->lay.bytes;
     const int threads = ctx->cells_per_cta * ctx->L;
     const int grid = ctx->num_sms * ctx->ctas_per_sm;
-    CU(cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned long long), ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_queue, 0, 4 * sizeof(unsigned long long), ctx->stream));
     void *k = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
     // the cells start after the cooling table in a mixed launch
     CellLayout lay = ctx->lay;
@@ -886,23 +918,6 @@ static ThreadArgs thread_args(sunb_ctx *ctx, double *y, double t0, double tout, 
     a.cool.n = ctx->nknots;
     a.cool.gamma_heat = ctx->gamma_heat;
     return a;
-}
-
-static int launch_thread(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
-{
-    ThreadArgs a = thread_args(ctx, y, t0, tout, status);
-    CU(cudaMemsetAsync(ctx->d_queue, 0, 2 * sizeof(unsigned long long), ctx->stream));
-    const int threads = 256;
-    void *k = ctx->kind == SUNB_ROBERTSON ? (void *)thread_kernel<RobertsonProblem>
-                                          : (void *)thread_kernel<CosmologyProblem>;
-    int occ = 0;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, threads, 0));
-    long long want = (ctx->C + threads - 1) / threads;
-    const int grid = (int)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ)));
-    void *args[] = {&a};
-    CU(cudaLaunchKernel(k, dim3(grid), dim3(threads), args, 0, ctx->stream));
-    ctx->launches++;
-    return SUNB_SUCCESS;
 }
 
 template <typename MT>
@@ -1010,39 +1025,75 @@ static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
     return SUNB_SUCCESS;
 }
 
-
-// Kernel configuration of one outer step (the same choice as launch_mech /
-// launch_thread), for the graph builder.
-static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status, void **func,
-                       dim3 &grid, dim3 &block, int &smem, MechArgs &ma, ThreadArgs &ta)
+// Thread-per-cell launch: 256 threads per CTA, as many CTAs as stay resident.
+static int thread_spec(sunb_ctx *ctx, const ThreadArgs &a, bool robertson, LaunchSpec &sp)
 {
+    sp.thread = true;
+    sp.ta = a;
+    sp.func = robertson ? (void *)thread_kernel<RobertsonProblem> : (void *)thread_kernel<CosmologyProblem>;
+    int occ = 0;
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp.func, 256, 0));
+    const long long want = (a.n + 255) / 256;
+    sp.grid = dim3((unsigned)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ))));
+    sp.block = dim3(256);
+    sp.smem = 0;
+    return SUNB_SUCCESS;
+}
+
+// The kernel launches of one outer step, which follow a reset of the cell
+// counters: one kernel, or for a mixed batch the mechanism kernel (with
+// cosmology cells in its tail) and then the cosmology thread kernel, which
+// takes the cosmology cells that are left from the same counter.
+static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status, LaunchSpec sp[2],
+                       int &n)
+{
+    n = 0;
     if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY) {
-        ta = thread_args(ctx, y, t0, tout, status);
-        *func = ctx->kind == SUNB_ROBERTSON ? (void *)thread_kernel<RobertsonProblem>
-                                            : (void *)thread_kernel<CosmologyProblem>;
-        int occ = 0;
-        CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, *func, 256, 0));
-        const long long want = (ctx->C + 255) / 256;
-        grid = dim3((unsigned)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ))));
-        block = dim3(256);
-        smem = 0;
-        return SUNB_SUCCESS;
+        n = 1;
+        return thread_spec(ctx, thread_args(ctx, y, t0, tout, status), ctx->kind == SUNB_ROBERTSON, sp[0]);
     }
     const bool cosmo = ctx->kind == SUNB_MIXED;
-    ma = mech_args(ctx, y, t0, tout, status);
+    LaunchSpec &m = sp[0];
+    m.thread = false;
+    m.ma = mech_args(ctx, y, t0, tout, status);
     if (cosmo) {
         const int shift = cool_bytes(ctx);
         CellLayout lay = ctx->lay;
         lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
         lay.sp += shift; lay.rq += shift; lay.dq += shift; lay.pm += shift;
-        ma.lay = lay;
-        ma.lay.bytes = ctx->lay.bytes;
-        ma.cool_smem_off = ctx->off.bytes;
+        m.ma.lay = lay;
+        m.ma.lay.bytes = ctx->lay.bytes;
+        m.ma.cool_smem_off = ctx->off.bytes;
     }
-    *func = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
-    smem = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0) + ctx->cells_per_cta * ctx->lay.bytes;
-    grid = dim3(ctx->num_sms * ctx->ctas_per_sm);
-    block = dim3(ctx->cells_per_cta * ctx->L);
+    m.func = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
+    m.smem = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0) + ctx->cells_per_cta * ctx->lay.bytes;
+    m.grid = dim3(ctx->num_sms * ctx->ctas_per_sm);
+    m.block = dim3(ctx->cells_per_cta * ctx->L);
+    n = 1;
+    if (cosmo) {
+        ThreadArgs ta = thread_args(ctx, y, t0, tout, status);
+        ta.n = ctx->Cc;
+        ta.queue = ctx->d_queue + 1;
+        ta.atol[0] = ctx->atol[ctx->off.N];
+        const int rc = thread_spec(ctx, ta, false, sp[1]);
+        if (rc != SUNB_SUCCESS) return rc;
+        n = 2;
+    }
+    return SUNB_SUCCESS;
+}
+
+static int launch_step(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
+{
+    LaunchSpec sp[2];
+    int n = 0;
+    const int rc = step_config(ctx, y, t0, tout, status, sp, n);
+    if (rc != SUNB_SUCCESS) return rc;
+    CU(cudaMemsetAsync(ctx->d_queue, 0, 4 * sizeof(unsigned long long), ctx->stream));
+    for (int i = 0; i < n; ++i) {
+        void *args[] = {sp[i].arg()};
+        CU(cudaLaunchKernel(sp[i].func, sp[i].grid, sp[i].block, args, sp[i].smem, ctx->stream));
+        ctx->launches++;
+    }
     return SUNB_SUCCESS;
 }
 
@@ -1207,13 +1258,13 @@ int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t
     if (!std::isfinite(t0) || !std::isfinite(tout) || tout < t0)
         return fail(ctx, SUNB_ILL_INPUT, "need finite t0 <= tout");
     if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)
-        return launch_thread(ctx, dev_y, t0, tout, dev_status);
+        return launch_step(ctx, dev_y, t0, tout, dev_status);
     ctx->replayed = false;
     if (ctx->autotune && !ctx->tuned && ctx->tune_cells > 0 && tout > t0) {
         const int rc = autotune(ctx, dev_y, t0, tout);
         if (rc != SUNB_SUCCESS) return rc;
     }
-    return launch_mech(ctx, dev_y, t0, tout, dev_status);
+    return launch_step(ctx, dev_y, t0, tout, dev_status);
 }
 
 int sunb_get_totals(sunb_ctx *ctx, sunb_totals *host_totals, int32_t *dev_cell_stats)
@@ -1399,36 +1450,43 @@ int sunb_graph_capture(sunb_ctx *ctx, double *dev_y, double t0, double dt, int32
     }
     if (ctx->graph_exec) { cudaGraphExecDestroy(ctx->graph_exec); ctx->graph_exec = nullptr; }
     if (ctx->graph) { cudaGraphDestroy(ctx->graph); ctx->graph = nullptr; }
-    ctx->graph_kernels.assign(nsteps, nullptr);
-    ctx->graph_margs.assign(nsteps, MechArgs{});
-    ctx->graph_targs.assign(nsteps, ThreadArgs{});
+    ctx->graph_kernels.clear();
+    ctx->graph_specs.clear();
+    ctx->graph_step.clear();
     CU(cudaGraphCreate(&ctx->graph, 0));
     cudaGraphNode_t prev = nullptr;
     for (int k = 0; k < nsteps; ++k) {
         const double a = t0 + k * dt, b = t0 + (k + 1) * dt;
-        int rc = step_config(ctx, dev_y, a, b, dev_status, &ctx->graph_func, ctx->graph_grid, ctx->graph_block,
-                             ctx->graph_smem, ctx->graph_margs[k], ctx->graph_targs[k]);
+        LaunchSpec sp[2];
+        int n = 0;
+        int rc = step_config(ctx, dev_y, a, b, dev_status, sp, n);
         if (rc != SUNB_SUCCESS) return rc;
         cudaMemsetParams mp{};
         mp.dst = ctx->d_queue;
         mp.value = 0;
         mp.elementSize = 4;
-        mp.width = 4;
+        mp.width = 8;              // the four 64-bit cell counters
         mp.height = 1;
         mp.pitch = 0;
         cudaGraphNode_t mnode;
         CU(cudaGraphAddMemsetNode(&mnode, ctx->graph, prev ? &prev : nullptr, prev ? 1 : 0, &mp));
-        cudaKernelNodeParams kp{};
-        kp.func = ctx->graph_func;
-        kp.gridDim = ctx->graph_grid;
-        kp.blockDim = ctx->graph_block;
-        kp.sharedMemBytes = ctx->graph_smem;
-        void *argp = (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)
-                         ? (void *)&ctx->graph_targs[k] : (void *)&ctx->graph_margs[k];
-        void *args[] = {argp};
-        kp.kernelParams = args;
-        CU(cudaGraphAddKernelNode(&ctx->graph_kernels[k], ctx->graph, &mnode, 1, &kp));
-        prev = ctx->graph_kernels[k];
+        prev = mnode;
+        for (int i = 0; i < n; ++i) {
+            ctx->graph_specs.push_back(sp[i]);
+            ctx->graph_step.push_back(k);
+            LaunchSpec &g = ctx->graph_specs.back();
+            cudaKernelNodeParams kp{};
+            kp.func = g.func;
+            kp.gridDim = g.grid;
+            kp.blockDim = g.block;
+            kp.sharedMemBytes = g.smem;
+            void *args[] = {g.arg()};
+            kp.kernelParams = args;
+            cudaGraphNode_t node;
+            CU(cudaGraphAddKernelNode(&node, ctx->graph, &prev, 1, &kp));
+            ctx->graph_kernels.push_back(node);
+            prev = node;
+        }
     }
     CU(cudaGraphInstantiate(&ctx->graph_exec, ctx->graph, 0));
     ctx->graph_dt = dt;
@@ -1440,18 +1498,17 @@ int sunb_graph_launch(sunb_ctx *ctx, double t0)
     if (!ctx) return SUNB_ILL_INPUT;
     if (!ctx->graph_exec) return fail(ctx, SUNB_ILL_INPUT, "no captured graph (sunb_graph_capture)");
     if (!std::isfinite(t0)) return fail(ctx, SUNB_ILL_INPUT, "t0 must be finite");
-    const bool thread = ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY;
     for (size_t k = 0; k < ctx->graph_kernels.size(); ++k) {
-        Controls &c = thread ? ctx->graph_targs[k].ctl : ctx->graph_margs[k].ctl;
-        c.t0 = t0 + (double)k * ctx->graph_dt;
-        c.tout = t0 + (double)(k + 1) * ctx->graph_dt;
+        LaunchSpec &g = ctx->graph_specs[k];
+        Controls &c = g.thread ? g.ta.ctl : g.ma.ctl;
+        c.t0 = t0 + (double)ctx->graph_step[k] * ctx->graph_dt;
+        c.tout = t0 + (double)(ctx->graph_step[k] + 1) * ctx->graph_dt;
         cudaKernelNodeParams kp{};
-        kp.func = ctx->graph_func;
-        kp.gridDim = ctx->graph_grid;
-        kp.blockDim = ctx->graph_block;
-        kp.sharedMemBytes = ctx->graph_smem;
-        void *argp = thread ? (void *)&ctx->graph_targs[k] : (void *)&ctx->graph_margs[k];
-        void *args[] = {argp};
+        kp.func = g.func;
+        kp.gridDim = g.grid;
+        kp.blockDim = g.block;
+        kp.sharedMemBytes = g.smem;
+        void *args[] = {g.arg()};
         kp.kernelParams = args;
         CU(cudaGraphExecKernelNodeSetParams(ctx->graph_exec, ctx->graph_kernels[k], &kp));
     }

@@ -81,22 +81,26 @@ __global__ void __launch_bounds__(256) robertson_noalloc_kernel(
 {
     unsigned long long *queue = reinterpret_cast<unsigned long long *>(scratch);
     int32_t *stats = reinterpret_cast<int32_t *>(scratch + 256);
-    for (;;) {
-        const long long cell = noalloc_grab(queue);
-        if (cell >= n) break;
-        ThreadCell<RobertsonProblem> tc;
-        tc.prob.load(k, cell);
-        tc.atol[0] = a0;
-        tc.atol[1] = a1;
-        tc.atol[2] = a2;
-        tc.yg = y + 3 * cell;
-        CellStats s;
-        bdf_cell(tc, ctl, s);
-        int4 *p = reinterpret_cast<int4 *>(stats + 8 * cell);
-        p[0] = make_int4(s.nst, s.nfe, s.nje, s.nni);
-        p[1] = make_int4(s.ncf, s.nef, s.qlast, s.status);
-        if (status) status[cell] = s.status;
-    }
+    ThreadCell<RobertsonProblem> tc;
+    tc.atol[0] = a0;
+    tc.atol[1] = a1;
+    tc.atol[2] = a2;
+    run_cells(
+        tc, ctl, launched_warp_mask(),
+        [&]() -> long long {
+            const long long cell = noalloc_grab(queue);
+            return cell < n ? cell : -1;
+        },
+        [&](long long cell) {
+            tc.prob.load(k, cell);
+            tc.yg = y + 3 * cell;
+        },
+        [&](long long cell, const CellStats &s) {
+            int4 *p = reinterpret_cast<int4 *>(stats + 8 * cell);
+            p[0] = make_int4(s.nst, s.nfe, s.nje, s.nni);
+            p[1] = make_int4(s.ncf, s.nef, s.qlast, s.status);
+            if (status) status[cell] = s.status;
+        });
 }
 
 }  // namespace
