@@ -122,14 +122,15 @@ __device__ __forceinline__ double eta_viable2(int p)
 }
 
 // The controller as a state machine that advances a cell by at most one
-// Newton iteration per call ("superstep").  Its phases -- STEP (start a
-// step), ATTEMPT (predict, coefficients), SETUP (f and the Newton matrix at
-// the prediction), NEWTON (one iteration: f, solve, convergence test) and
-// POST (Newton failure, error test, accept, step and order selection) --
-// are visited in this fixed order inside a superstep.  Cells that share a
-// warp (a thread per cell, or several lane groups per warp) therefore reach
-// the one right-hand-side call of NEWTON and the one set-up call of SETUP
-// together, whatever their step counts, instead of diverging through
+// step attempt (or, for backends that ask for it, one Newton iteration) per
+// call ("superstep").  Its phases -- STEP (start a step),
+// ATTEMPT (predict, coefficients), SETUP (f and the Newton matrix at the
+// prediction), NEWTON (the iterations: f, solve, convergence test) and POST
+// (Newton failure, error test, accept, step and order selection) -- are
+// visited in this fixed order inside a superstep.  Cells that share a warp
+// (a thread per cell, or several lane groups per warp) therefore run the
+// right-hand-side call of NEWTON, the set-up call of SETUP and the control
+// logic together, whatever their step counts, instead of diverging through
 // nested loops.  A cell's arithmetic is exactly that of the sequential
 // algorithm (bdf_cell below runs it sequentially).
 enum Phase : int {
@@ -277,7 +278,10 @@ struct CellRun {
             fcur = 1;                                        // V_F holds f(z0)
             start_newton(c);
         }
-        if (phase == PH_NEWTON) {     // one modified-Newton iteration (Eq. stop_newton)
+        // modified Newton iterations (Eq. stop_newton) until convergence,
+        // divergence or MAXCOR: all of them in this superstep when the
+        // backend asks for it (C::kNewtonLoop), else one per superstep
+        while (phase == PH_NEWTON) {
             if (!fcur) { c.rhs(V_Y, V_F); s.nfe++; }
             fcur = 0;
             s.nni++;
@@ -295,6 +299,7 @@ struct CellRun {
                 else { delp2 = dn2; ++m; }
             }
             if (done) phase = PH_POST;
+            if (!C::kNewtonLoop) break;
         }
         if (phase == PH_POST) post(c);
     }

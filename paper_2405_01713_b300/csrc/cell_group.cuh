@@ -225,6 +225,10 @@ __host__ __device__ __forceinline__ int tape_record(int N) { return N + 46; }
 
 template <int L, typename MT>
 struct GroupCell {
+    // one Newton iteration per superstep: a group that needs another
+    // iteration takes it in the next superstep, at the same f call site as
+    // the first iterations of the other groups of its warp
+    static constexpr bool kNewtonLoop = false;
     Grp<L> g;
     MechTab tb;
     int N, K, M, NP;

@@ -92,6 +92,9 @@ struct CosmologyProblem {
 template <class Prob>
 struct ThreadCell {
     static constexpr int N = Prob::N;
+    // all Newton iterations of an attempt in one superstep: the control
+    // logic (cheap f, costly control) then stays aligned across the warp
+    static constexpr bool kNewtonLoop = true;
     Prob prob;
     double v[NVEC][N];
     double M[N][N];
