@@ -170,7 +170,7 @@ int sunb_lu_solve_batched(int32_t n, int64_t batch, double *dev_A, int32_t *dev_
 int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *dev_piv,
                               float *dev_b, int32_t *dev_info, void *stream);
 
-/* Discrete adjoint (spec differentiation extension; the paper only
+/* Discrete adjoint (a differentiation extension of the path; the paper only
  * names the sensitivity-capable packages CVODES/IDAS, Sec. 2).  With
  * record_adjoint = cap > 0 at create, sunb_integrate records per cell and
  * accepted step the state, the Nordsieck column map applied since the

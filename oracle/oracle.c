@@ -654,7 +654,7 @@ EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int 
     return 0;
 }
 
-/* ---- discrete adjoint (the spec differentiation extension) --------
+/* ---- discrete adjoint (differentiation through the integrator) ---------
  * Gradient of a loss on the final state with respect to the Arrhenius
  * parameters (ln A_j, Ea_j) of the frozen forward map recorded on the tape
  * (see orc_tape).  Reverse sweep: lam is the adjoint of the Nordsieck array;

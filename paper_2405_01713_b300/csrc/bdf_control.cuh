@@ -153,7 +153,7 @@ struct CellRun {
     double dsm2, Cq, il1, gamma;
     double l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1];
     // current Newton solve
-    int fresh, conv, fcur, m;
+    int fresh, conv, setup_now, m;
     double delp2, R2, cstale;
 
     __device__ void finish(C &c)
@@ -212,7 +212,6 @@ struct CellRun {
 
     __device__ void start_newton(C &c)
     {
-        if (!have_M) { conv = 0; phase = PH_POST; return; }
         c.newton_init();
         delp2 = 0.0;
         R2 = 1.0;
@@ -263,7 +262,7 @@ struct CellRun {
             }
             gamma = h * il1;
             fresh = 0;
-            fcur = 0;
+            setup_now = 0;
             if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
                 fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX)
                 phase = PH_SETUP;
@@ -271,32 +270,37 @@ struct CellRun {
                 start_newton(c);
         }
         if (phase == PH_SETUP) {
-            have_M = c.rhs_setup(V_Z0, V_F, gamma);
+            // the Newton matrix at the prediction z0: built by the first
+            // Newton iteration below, whose f evaluation is at y = z0
             s.nje++;
-            s.nfe++;
             gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; force_setup = 0;
-            fcur = 1;                                        // V_F holds f(z0)
+            setup_now = 1;
             start_newton(c);
         }
         // modified Newton iterations (Eq. stop_newton) until convergence,
         // divergence or MAXCOR: all of them in this superstep when the
         // backend asks for it (C::kNewtonLoop), else one per superstep
         while (phase == PH_NEWTON) {
-            if (!fcur) { c.rhs(V_Y, V_F); s.nfe++; }
-            fcur = 0;
-            s.nni++;
-            c.newton_residual(h, il1);
-            c.solve(V_DEL);
-            const double dn2 = c.newton_update(cstale);
+            const int ok = c.newton_f(setup_now != 0, gamma);
+            s.nfe++;
+            if (setup_now) { have_M = ok; setup_now = 0; }
             bool done = false;
             conv = 0;
-            if (!(dn2 <= 1.7e308)) {
-                done = true;                                 // not finite
+            if (!have_M) {
+                done = true;                                 // singular matrix
             } else {
-                if (m > 0) R2 = fmax(CRDOWN * CRDOWN * R2, dn2 * rcp(delp2));
-                if (R2 * dn2 * (Cq * Cq) < NLS_COEF * NLS_COEF) { conv = 1; done = true; }
-                else if (m + 1 == MAXCOR || (m > 0 && dn2 > RDIV * RDIV * delp2)) done = true;
-                else { delp2 = dn2; ++m; }
+                s.nni++;
+                c.newton_residual(h, il1);
+                c.solve(V_DEL);
+                const double dn2 = c.newton_update(cstale);
+                if (!(dn2 <= 1.7e308)) {
+                    done = true;                             // not finite
+                } else {
+                    if (m > 0) R2 = fmax(CRDOWN * CRDOWN * R2, dn2 * rcp(delp2));
+                    if (R2 * dn2 * (Cq * Cq) < NLS_COEF * NLS_COEF) { conv = 1; done = true; }
+                    else if (m + 1 == MAXCOR || (m > 0 && dn2 > RDIV * RDIV * delp2)) done = true;
+                    else { delp2 = dn2; ++m; }
+                }
             }
             if (done) phase = PH_POST;
             if (!C::kNewtonLoop) break;

@@ -238,7 +238,8 @@ struct GroupCell {
     int32_t *perm;        // [N] row permutation of the factorisation
     MT *xs;               // [N] solve scratch
     MT *dinv;             // [N] reciprocal pivots
-    double *C, *eg, *egi, *hRT, *cpR, *wdot, *u, *wT;   // species scratch ([K+1] for the first three)
+    double *C, *D, *egi, *hRT, *cpR, *wdot, *u, *wT;    // species scratch ([K+1] for the first four);
+                                                        // D_k = exp(g_k) C_k, egi_k = exp(-g_k)
     double *q;                                          // [M]
     MT *dq;                                             // [6M] gamma dq_j/dC at each position
     double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
@@ -261,7 +262,7 @@ struct GroupCell {
         xs = reinterpret_cast<MT *>(base + lay.xs);
         dinv = xs + N;
         double *sp = reinterpret_cast<double *>(base + lay.sp);
-        C = sp; eg = C + (K + 1); egi = eg + (K + 1); hRT = egi + (K + 1);
+        C = sp; D = C + (K + 1); egi = D + (K + 1); hRT = egi + (K + 1);
         cpR = hRT + (K + 1); wdot = cpR + K; u = wdot + K; wT = u + K;
         q = reinterpret_cast<double *>(base + lay.rq);
         dq = reinterpret_cast<MT *>(base + lay.dq);
@@ -269,7 +270,7 @@ struct GroupCell {
         uq = dqdT + M;
         Pm = reinterpret_cast<double *>(base + lay.pm);
         wmu = Pm + 36;
-        if (g.lane == 0) { C[K] = 1.0; eg[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; wmu[K] = 0.0; }
+        if (g.lane == 0) { C[K] = 1.0; D[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; wmu[K] = 0.0; }
         g.sync();
     }
 
@@ -511,8 +512,10 @@ struct GroupCell {
     }
 
     // ---------------- right-hand side (+ Newton matrix) ----------------
-    template <bool JAC>
-    __device__ int eval(int sin, int sout, double gamma, bool add_identity = true)
+    // f(y) of slot sin into slot sout; with jac also M = I - gamma J(y) (or
+    // -gamma J without the identity) into mat.  jac is uniform over the
+    // group; groups of a warp with and without it share the f part.
+    __device__ int eval(int sin, int sout, double gamma, bool jac, bool add_identity = true)
     {
         const double *y = V(sin);
         double *f = V(sout);
@@ -530,8 +533,9 @@ struct GroupCell {
             const double hrt = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
             const double sr = ss[0] * lnT + T * (ss[1] + T * (ss[2] + T * (ss[3] + T * ss[4]))) + ss[5];
             const double e = exp(hrt - sr);
-            C[k] = rho * y[k] * tb.invW[k];
-            eg[k] = e;
+            const double ck = rho * y[k] * tb.invW[k];
+            C[k] = ck;
+            D[k] = e * ck;
             egi[k] = rcp(e);
             hRT[k] = hrt;
             cpR[k] = cp;
@@ -545,20 +549,26 @@ struct GroupCell {
             const int p1 = b & 0xff, p2 = (b >> 8) & 0xff, dnu = (int)((b >> 16) & 0xff) - 8;
             const double *rp = tb.rpar + 3 * j;
             const double kf = exp(rp[0] + rp[1] * lnT - rp[2] * invT);
-            const double kr = kf * (egi[r0] * egi[r1] * egi[r2]) * (eg[p0] * eg[p1] * eg[p2]) * pw[dnu + 2];
+            // kr prod_p C_p = kf / Kc prod_p C_p = kf * G * B with
+            // G = prod_r exp(-g_r) (P_atm/RT)^-dnu and B = prod_p exp(g_p) C_p
             const double c0 = C[r0], c1 = C[r1], c2 = C[r2];
-            const double d0 = C[p0], d1 = C[p1], d2 = C[p2];
-            const double fwd = kf * (c0 * c1 * c2), rev = kr * (d0 * d1 * d2);
-            q[j] = fwd - rev;
-            if (JAC) {
+            const double A = c0 * c1 * c2;
+            const double G = (egi[r0] * egi[r1] * egi[r2]) * pw[dnu + 2];
+            const double B = D[p0] * D[p1] * D[p2];
+            q[j] = kf * (A - G * B);
+            if (jac) {
                 MT *dj = dq + 6 * j;
-                const double gkf = gamma * kf, gkr = gamma * kr;
+                const double rkf = kf * G;                 // kr = rkf prod_p exp(g_p)
+                const double fwd = kf * A, rev = rkf * B;
+                const double gkf = gamma * kf, grk = gamma * rkf;
+                const double D0 = D[p0], D1 = D[p1], D2 = D[p2];
                 dj[0] = (MT)(gkf * (c1 * c2));
                 dj[1] = (MT)(gkf * (c0 * c2));
                 dj[2] = (MT)(gkf * (c0 * c1));
-                dj[3] = (MT)(-gkr * (d1 * d2));
-                dj[4] = (MT)(-gkr * (d0 * d2));
-                dj[5] = (MT)(-gkr * (d0 * d1));
+                // gamma kr prod_{p != i} C_p = gamma rkf exp(g_i) prod_{p != i} D_p
+                dj[3] = (MT)(-grk * rcp(egi[p0]) * (D1 * D2));
+                dj[4] = (MT)(-grk * rcp(egi[p1]) * (D0 * D2));
+                dj[5] = (MT)(-grk * rcp(egi[p2]) * (D0 * D1));
                 const double af = rp[1] + rp[2] * invT;
                 const double dH = (hRT[p0] + hRT[p1] + hRT[p2]) - (hRT[r0] + hRT[r1] + hRT[r2]);
                 dqdT[j] = gamma * invT * (af * fwd - (af - dH + (double)dnu) * rev);
@@ -578,7 +588,7 @@ struct GroupCell {
             f[k] = wd * tb.W[k] * rrho;
             hw += hRT[k] * wd;
             cpm += y[k] * cpR[k] * tb.invW[k];
-            if (JAC) wdot[k] = wd;
+            if (jac) wdot[k] = wd;
         }
         hw = g.sum(hw);
         cpm = g.sum(cpm);
@@ -588,7 +598,7 @@ struct GroupCell {
         last_cpm = cpm;
         last_T = T;
         g.sync();
-        if (!JAC) return 1;
+        if (!jac) return 1;
 
         // ---- Newton matrix M = I - gamma J (gamma folded into dq, dqdT) ----
         // rows k < K of gamma*Jc (in MT), and gamma * dwdot/dT, gamma * u (in FP64)
@@ -662,11 +672,20 @@ struct GroupCell {
         return 1;
     }
 
-    __device__ __forceinline__ void rhs(int a, int b) { eval<false>(a, b, 0.0); }
+    __device__ __forceinline__ void rhs(int a, int b) { eval(a, b, 0.0, false); }
     __device__ __forceinline__ int rhs_setup(int a, int b, double gamma)
     {
-        eval<true>(a, b, gamma);
+        eval(a, b, gamma, true);
         return factor();
+    }
+    // The f evaluation of a Newton iteration, f(y) into V_F; with setup also
+    // the Newton matrix at y, factored (0: singular).  One call site for
+    // both, so groups of a warp that set up and groups that do not share
+    // the right-hand-side work.
+    __device__ __forceinline__ int newton_f(bool setup, double gamma)
+    {
+        eval(V_Y, V_F, gamma, setup);
+        return setup ? factor() : 1;
     }
 
     __device__ int factor() { return lu_factor<L, MT>(g, mat, N, perm, dinv, nullptr); }

@@ -267,6 +267,14 @@ struct ThreadCell {
         }
         return s * (1.0 / N);
     }
+    // the f evaluation of a Newton iteration, f(y) into V_F; with setup also
+    // the Newton matrix at y, factored (0: singular)
+    __device__ __forceinline__ int newton_f(bool setup, double gamma)
+    {
+        if (setup) return rhs_setup(V_Y, V_F, gamma);
+        rhs(V_Y, V_F);
+        return 1;
+    }
     // f(z0) into slot fo, J at z0, M = I - gamma J, in-register LU with row
     // partial pivoting (first index of largest magnitude).  Pivots are kept
     // as an explicit permutation applied in solve().

@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(128) mech_eval_kernel(const MechArgs a, const 
             c.rhs(V_Y, V_F);
             for (int i = c.g.lane; i < N; i += 32) out[cell * N + i] = c.V(V_F)[i];
         } else {
-            c.template eval<true>(V_Y, V_F, -1.0, false);
+            c.eval(V_Y, V_F, -1.0, true, false);
             for (int i = c.g.lane; i < N * N; i += 32) out[cell * N * N + i] = (double)c.mat[i];
         }
         c.g.sync();
@@ -422,7 +422,7 @@ __global__ void __launch_bounds__(128) adjoint_replay_kernel(const AdjArgs a)
             c.g.sync();
             c.predict(q);
             for (int it = 0; it < 12; ++it) {             // full Newton, exact J
-                c.template eval<true>(V_Y, V_F, gamma);
+                c.eval(V_Y, V_F, gamma, true);
                 if (!c.factor()) break;
                 for (int i = c.g.lane; i < N; i += L)
                     d[i] = -(y[i] - gamma * f[i] - (z0[i] - il1 * c.vec[c.NP + i]));
@@ -492,7 +492,7 @@ __global__ void __launch_bounds__(128) adjoint_reverse_kernel(const AdjArgs a)
                 y[i] = rec[i];
             }
             c.g.sync();
-            c.template eval<true>(V_Y, V_F, gamma);       // M = I - gamma J(y_n)
+            c.eval(V_Y, V_F, gamma, true);       // M = I - gamma J(y_n)
             c.factor();
             lu_solve_t<L>(c.g, c.mat, N, c.perm, c.dinv, c.xs, ld);   // mu
             adj_theta<L>(c, ld, gamma, g);

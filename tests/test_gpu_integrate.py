@@ -67,7 +67,7 @@ def test_robertson_full_config():
 def test_mechanism22_mappings_and_precisions(lanes, precision):
     """Every lanes-per-cell mapping and both matrix precisions solve the
     same problem to the method's accuracy; the FP32 Newton matrix only
-    changes the iteration, not the error control (spec mixed form)."""
+    changes the iteration, not the error control (the mixed-precision form)."""
     need_gpu()
     w = synth.workloads.mech22(97)
     yg, cs, tot, it = run_gpu(w, lanes=lanes, precision=precision, max_steps=20000)
