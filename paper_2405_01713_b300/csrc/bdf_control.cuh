@@ -269,9 +269,11 @@ struct CellRun {
             else
                 start_newton(c);
         }
-        if (phase == PH_SETUP) {
-            // the Newton matrix at the prediction z0: built by the first
-            // Newton iteration below, whose f evaluation is at y = z0
+        // the Newton matrix at the prediction z0: built by the first Newton
+        // iteration below, whose f evaluation is at y = z0.  A backend whose
+        // set-up scratch is taken by another cell of the warp defers the
+        // set-up to the next superstep.
+        if (phase == PH_SETUP && c.acquire_setup()) {
             s.nje++;
             gamma_M = gamma; nst_lastsetup = s.nst; fresh = 1; force_setup = 0;
             setup_now = 1;

@@ -41,7 +41,9 @@ struct MechTabOffsets {
     int bytes;                                           // blob size (multiple of 16)
 };
 
-// Per-cell shared-memory layout (byte offsets from the cell's base).
+// Per-cell shared-memory layout (byte offsets from the cell's base; dq < 0:
+// the Newton-matrix scratch lives outside the cell and is set by
+// set_jac_scratch, pm < 0: no adjoint map).
 struct CellLayout {
     int NP;            // padded vector length
     int vec, mat, perm, xs, sp, rq, dq, pm, bytes;   // xs: 2N MT (solve scratch, reciprocal pivots);
@@ -244,6 +246,7 @@ struct GroupCell {
     MT *dq;                                             // [6M] gamma dq_j/dC at each position
     double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
     double *yg;
+    int *jac_lock = nullptr;   // non-null: dq/dqdT/uq shared with the other groups of the warp
     // discrete-adjoint recording (null tape: no recording)
     double *tape = nullptr;
     int tape_cap = 0, rec_count = 0;
@@ -265,13 +268,47 @@ struct GroupCell {
         C = sp; D = C + (K + 1); egi = D + (K + 1); hRT = egi + (K + 1);
         cpR = hRT + (K + 1); wdot = cpR + K; u = wdot + K; wT = u + K;
         q = reinterpret_cast<double *>(base + lay.rq);
-        dq = reinterpret_cast<MT *>(base + lay.dq);
-        dqdT = reinterpret_cast<double *>(base + lay.dq + ((6 * M * (int)sizeof(MT) + 15) & ~15));
-        uq = dqdT + M;
-        Pm = reinterpret_cast<double *>(base + lay.pm);
-        wmu = Pm + 36;
-        if (g.lane == 0) { C[K] = 1.0; D[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0; wmu[K] = 0.0; }
+        if (lay.dq >= 0) set_jac_scratch(base + lay.dq, nullptr);
+        if (lay.pm >= 0) {
+            Pm = reinterpret_cast<double *>(base + lay.pm);
+            wmu = Pm + 36;
+        } else {
+            Pm = wmu = nullptr;
+        }
+        if (g.lane == 0) {
+            C[K] = 1.0; D[K] = 1.0; egi[K] = 1.0; hRT[K] = 0.0;
+            if (wmu) wmu[K] = 0.0;
+        }
         g.sync();
+    }
+
+    // Newton-matrix scratch: dq [6M] in MT, then dqdT and uq [M] in FP64
+    // (jac_scratch_bytes).  With a lock, the groups of a warp share one
+    // scratch: a group takes it before a set-up (acquire_setup) and gives
+    // it back once its matrix is assembled, within one superstep, so no
+    // group ever waits for it.
+    __device__ void set_jac_scratch(unsigned char *p, int *lock)
+    {
+        dq = reinterpret_cast<MT *>(p);
+        dqdT = reinterpret_cast<double *>(p + ((6 * M * (int)sizeof(MT) + 15) & ~15));
+        uq = dqdT + M;
+        jac_lock = lock;
+    }
+    __device__ __forceinline__ bool acquire_setup()
+    {
+        if (!jac_lock) return true;
+        int got = 0;
+        if (g.lane == 0) got = (atomicCAS(jac_lock, 0, 1) == 0);
+        return __shfl_sync(g.mask, got, 0, L) != 0;
+    }
+    __device__ __forceinline__ void release_setup()
+    {
+        if (!jac_lock) return;
+        g.sync();
+        if (g.lane == 0) {
+            __threadfence_block();
+            atomicExch(jac_lock, 0);
+        }
     }
 
     // ---------------- adjoint tape ----------------
@@ -685,7 +722,9 @@ struct GroupCell {
     __device__ __forceinline__ int newton_f(bool setup, double gamma)
     {
         eval(V_Y, V_F, gamma, setup);
-        return setup ? factor() : 1;
+        if (!setup) return 1;
+        release_setup();                 // the matrix is assembled: scratch free
+        return factor();
     }
 
     __device__ int factor() { return lu_factor<L, MT>(g, mat, N, perm, dinv, nullptr); }

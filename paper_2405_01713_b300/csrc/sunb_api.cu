@@ -82,6 +82,8 @@ struct MechArgs {
     double *tape;
     long long tape_stride;
     int tape_cap;
+    // Newton-matrix scratch shared per warp (mech_kernel; dq_off < 0: in the cell)
+    int dq_off, dq_bytes, lock_off;
 };
 
 __device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned char *src, int bytes)
@@ -128,6 +130,9 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
     stage_bytes(smem, a.tab, a.off.bytes);
     CoolingSmem cool;
     if (COSMO) cool = stage_cooling(smem + a.cool_smem_off, a.cool);
+    int *locks = reinterpret_cast<int *>(smem + a.lock_off);
+    if (a.dq_off >= 0)
+        for (int i = threadIdx.x; i < (int)(blockDim.x + 31) / 32; i += blockDim.x) locks[i] = 0;
     __syncthreads();
 
     const int gid = threadIdx.x / L;
@@ -138,6 +143,10 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
     c.N = a.off.N; c.K = a.off.K; c.M = a.off.M;
     c.invN = a.invN;
     c.bind(smem + a.off.bytes + gid * a.lay.bytes, a.lay);
+    if (a.dq_off >= 0) {   // one Newton-matrix scratch per warp, locked when groups share it
+        const int w = threadIdx.x >> 5;
+        c.set_jac_scratch(smem + a.dq_off + w * a.dq_bytes, L < 32 ? locks + w : nullptr);
+    }
 
     const unsigned wmask = launched_warp_mask();
     long long next = (long long)blockIdx.x * a.cells_per_cta + gid;
@@ -750,7 +759,11 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     return SUNB_SUCCESS;
 }
 
-static CellLayout make_layout(int N, int K, int M, int mt)
+// Bytes of one Newton-matrix scratch: dq [6M] in the matrix type, then
+// dqdT and uq [M] in FP64 (GroupCell::set_jac_scratch).
+static int jac_scratch_bytes(int M, int mt) { return align16(mt * 6 * M) + 16 * M; }
+
+static CellLayout make_layout(int N, int K, int M, int mt, bool dq_in_cell = true, bool with_pm = true)
 {
     CellLayout l{};
     l.NP = (N + 1) & ~1;
@@ -762,9 +775,20 @@ static CellLayout make_layout(int N, int K, int M, int mt)
     l.xs = take(mt * 2 * N);
     l.sp = take(8 * (4 * (K + 1) + 4 * K));
     l.rq = take(8 * M);
-    l.dq = take(align16(mt * 6 * M) + 8 * 2 * M);   // dq (MT), then dq/dT and u terms (FP64)
-    l.pm = take(8 * (36 + K + 1));                  // adjoint column map and scratch
+    l.dq = dq_in_cell ? take(jac_scratch_bytes(M, mt)) : -1;
+    l.pm = with_pm ? take(8 * (36 + K + 1)) : -1;   // adjoint column map and scratch
     l.bytes = off;
+    return l;
+}
+
+// The cell fields of a layout moved by shift bytes (cells placed after the
+// cooling table of a mixed launch).
+static CellLayout shifted(CellLayout l, int shift)
+{
+    l.vec += shift; l.mat += shift; l.perm += shift; l.xs += shift;
+    l.sp += shift; l.rq += shift;
+    if (l.dq >= 0) l.dq += shift;
+    if (l.pm >= 0) l.pm += shift;
     return l;
 }
 
@@ -784,20 +808,38 @@ static void *pick_mech_kernel(int L, int precision, bool cosmo)
 
 static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(8 * 3 * c->nknots) : 0; }
 
+// Shared memory of a mechanism CTA with c cells of L lanes: the tables, the
+// cooling table (mixed launches), the cells, one Newton-matrix scratch per
+// warp, and the warps' scratch locks.
+struct MechSmem {
+    int cells_off, dq_off, dq_bytes, lock_off, bytes;
+};
+static MechSmem mech_smem(const sunb_ctx *ctx, int c, int L)
+{
+    MechSmem m;
+    const int mt = ctx->precision == SUNB_MIXED32 ? 4 : 8;
+    const int warps = (c * L + 31) / 32;
+    m.cells_off = ctx->off.bytes + (ctx->kind == SUNB_MIXED ? cool_bytes(ctx) : 0);
+    m.dq_bytes = jac_scratch_bytes(ctx->off.M, mt);
+    m.dq_off = m.cells_off + c * ctx->lay.bytes;
+    m.lock_off = m.dq_off + warps * m.dq_bytes;
+    m.bytes = m.lock_off + align16(4 * warps);
+    return m;
+}
+
 // Cells per CTA for lanes-per-cell L: the count that keeps the most cells
-// resident per SM within the shared-memory budget (whole warps, <= 1024 threads).
+// resident per SM within the shared-memory budget (whole warps, <= 256 threads).
 static int configure_mech(sunb_ctx *ctx, int L, int force_cpc = 0)
 {
     const int mt = ctx->precision == SUNB_MIXED32 ? 4 : 8;
-    ctx->lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, mt);
+    ctx->lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, mt, false, ctx->tape_cap > 0);
     const bool cosmo = ctx->kind == SUNB_MIXED;
     int dev_optin = 0, sm_bytes = 0;
     CU(cudaDeviceGetAttribute(&dev_optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
     CU(cudaDeviceGetAttribute(&sm_bytes, cudaDevAttrMaxSharedMemoryPerMultiprocessor, ctx->device));
-    const int fixed = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0);
     int best_c = 0, best_res = -1;
     for (int c = std::max(1, 32 / L); c * L <= 256; c += std::max(1, 32 / L)) {
-        const int bytes = fixed + c * ctx->lay.bytes;
+        const int bytes = mech_smem(ctx, c, L).bytes;
         if (bytes > dev_optin) break;
         int blocks = sm_bytes / (bytes + 1024);
         blocks = std::min(blocks, 2048 / (c * L));
@@ -807,13 +849,13 @@ static int configure_mech(sunb_ctx *ctx, int L, int force_cpc = 0)
     if (best_c == 0)
         return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for shared memory at this precision and mapping");
     if (force_cpc > 0) {
-        if (force_cpc * L > 256 || (force_cpc * L) % 32 != 0 || fixed + force_cpc * ctx->lay.bytes > dev_optin)
+        if (force_cpc * L > 256 || (force_cpc * L) % 32 != 0 || mech_smem(ctx, force_cpc, L).bytes > dev_optin)
             return fail(ctx, SUNB_ILL_INPUT, "cells per CTA does not fit");
         best_c = force_cpc;
     }
     ctx->L = L;
     ctx->cells_per_cta = best_c;
-    const int bytes = fixed + best_c * ctx->lay.bytes;
+    const int bytes = mech_smem(ctx, best_c, L).bytes;
     void *k = pick_mech_kernel(L, ctx->precision, cosmo);
     CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     int occ = 0;
@@ -840,6 +882,10 @@ static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int3
     a.tape = ctx->d_tape;
     a.tape_stride = ctx->tape_stride;
     a.tape_cap = ctx->tape_cap;
+    const MechSmem ms = mech_smem(ctx, ctx->cells_per_cta, ctx->L);
+    a.dq_off = ms.dq_off;
+    a.dq_bytes = ms.dq_bytes;
+    a.lock_off = ms.lock_off;
     const bool mixed = ctx->kind == SUNB_MIXED;
     a.n_mech = ctx->C;
     a.y_mech = y ? y + (mixed ? ctx->Cc : 0) : nullptr;
@@ -857,6 +903,7 @@ static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int3
         a.cool.gamma_heat = ctx->gamma_heat;
         a.atol_cosmo = ctx->atol[ctx->off.N];
         a.cool_smem_off = ctx->off.bytes;
+        a.lay = shifted(ctx->lay, cool_bytes(ctx));   // the cells follow the cooling table
     }
     return a;
 }
@@ -873,26 +920,11 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
         a.n_cosmo = 0;
         a.tape = nullptr;
     }
-    if (cosmo) {   // mechanism tables, cooling table, then the cells
-        a.cool_smem_off = ctx->off.bytes;
-        a.off.bytes = ctx->off.bytes;
-    }
-    const int fixed = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0);
-    const int bytes = fixed + ctx->cells_per_cta * ctx->lay.bytes;
+    const int bytes = mech_smem(ctx, ctx->cells_per_cta, ctx->L).bytes;
     const int threads = ctx->cells_per_cta * ctx->L;
     const int grid = ctx->num_sms * ctx->ctas_per_sm;
     CU(cudaMemsetAsync(ctx->d_queue, 0, 4 * sizeof(unsigned long long), ctx->stream));
     void *k = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
-    // the cells start after the cooling table in a mixed launch
-    CellLayout lay = ctx->lay;
-    if (cosmo) {
-        const int shift = cool_bytes(ctx);
-        // GroupCell::bind takes offsets from (tables + gid * cell bytes); shift every field
-        lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
-        lay.sp += shift; lay.rq += shift; lay.dq += shift; lay.pm += shift;
-        a.lay = lay;
-        a.lay.bytes = ctx->lay.bytes;
-    }
     void *args[] = {&a};
     CU(cudaLaunchKernel(k, dim3(grid), dim3(threads), args, bytes, ctx->stream));
     ctx->launches++;
@@ -1056,17 +1088,8 @@ static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
     LaunchSpec &m = sp[0];
     m.thread = false;
     m.ma = mech_args(ctx, y, t0, tout, status);
-    if (cosmo) {
-        const int shift = cool_bytes(ctx);
-        CellLayout lay = ctx->lay;
-        lay.vec += shift; lay.mat += shift; lay.perm += shift; lay.xs += shift;
-        lay.sp += shift; lay.rq += shift; lay.dq += shift; lay.pm += shift;
-        m.ma.lay = lay;
-        m.ma.lay.bytes = ctx->lay.bytes;
-        m.ma.cool_smem_off = ctx->off.bytes;
-    }
     m.func = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
-    m.smem = ctx->off.bytes + (cosmo ? cool_bytes(ctx) : 0) + ctx->cells_per_cta * ctx->lay.bytes;
+    m.smem = mech_smem(ctx, ctx->cells_per_cta, ctx->L).bytes;
     m.grid = dim3(ctx->num_sms * ctx->ctas_per_sm);
     m.block = dim3(ctx->cells_per_cta * ctx->L);
     n = 1;
@@ -1173,9 +1196,9 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
         if (cudaMemcpy(ctx->d_tab, ctx->blob.data(), ctx->off.bytes, cudaMemcpyHostToDevice) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "copy tables"); return bail(SUNB_CUDA_ERROR); }
         int L = lpc ? lpc : (ctx->off.N > 32 ? 32 : 16);
         ctx->autotune = lpc == 0;
+        ctx->tape_cap = prob->record_adjoint > 0 ? prob->record_adjoint : 0;   // cells keep the adjoint map
         if ((rc = configure_mech(ctx, L)) != SUNB_SUCCESS) return bail(rc);
         if (prob->record_adjoint) {
-            ctx->tape_cap = prob->record_adjoint;
             ctx->tape_stride = tape_header(ctx->N) + (long long)ctx->tape_cap * tape_record(ctx->N);
             if (cudaMalloc(&ctx->d_tape, 8 * (size_t)ctx->tape_stride * ctx->C) != cudaSuccess ||
                 cudaMalloc(&ctx->d_gcells, 8 * 2 * (size_t)ctx->off.M * ctx->C) != cudaSuccess ||
