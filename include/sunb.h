@@ -170,6 +170,14 @@ int sunb_lu_solve_batched(int32_t n, int64_t batch, double *dev_A, int32_t *dev_
 int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *dev_piv,
                               float *dev_b, int32_t *dev_info, void *stream);
 
+/* The exponential that the right-hand-side kernels use (a table-driven
+ * method after Tang 1989: 64-entry table of 2^(j/64), degree-5 polynomial
+ * on |r| <= ln2/128; the library exp for |x| >= 704 and NaN), applied to
+ * dev_x [n] into dev_y [n] on the given stream; returns after the result is
+ * written.  For checking its accuracy against exp.  SUNB_ILL_INPUT for
+ * n < 0 or NULL arrays with n > 0 (message via sunb_last_error(NULL)). */
+int sunb_exp_check(const double *dev_x, double *dev_y, int64_t n, void *stream);
+
 /* Discrete adjoint (a differentiation extension of the path; the paper only
  * names the sensitivity-capable packages CVODES/IDAS, Sec. 2).  With
  * record_adjoint = cap > 0 at create, sunb_integrate records per cell and

@@ -38,6 +38,7 @@ struct MechTabOffsets {
     int K, M, N, nnz;
     int invW, W, cpc, hc, sc, dcp, rpar, atol, inc_nu;   // double arrays
     int ridx, inc_ptr, inc_j, inc_nuf, invWf;            // 32-bit arrays
+    int exptab;                                          // the exp table (EXP_TABLE_SIZE doubles)
     int bytes;                                           // blob size (multiple of 16)
 };
 
@@ -56,6 +57,7 @@ struct MechTab {
     const uint32_t *ridx;
     const int32_t *inc_ptr, *inc_j;
     const float *inc_nuf, *invWf;          // FP32 copies for the FP32 Newton matrix
+    const double *exptab;                  // 2^(j/64), for fexp
     template <typename T> __device__ __forceinline__ const T *nu() const;
     template <typename T> __device__ __forceinline__ const T *iw() const;
 };
@@ -82,6 +84,7 @@ __device__ __forceinline__ MechTab mech_tab_at(const unsigned char *base, const 
     t.inc_j = reinterpret_cast<const int32_t *>(base + o.inc_j);
     t.inc_nuf = reinterpret_cast<const float *>(base + o.inc_nuf);
     t.invWf = reinterpret_cast<const float *>(base + o.invWf);
+    t.exptab = reinterpret_cast<const double *>(base + o.exptab);
     return t;
 }
 
@@ -569,7 +572,7 @@ struct GroupCell {
             const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
             const double hrt = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
             const double sr = ss[0] * lnT + T * (ss[1] + T * (ss[2] + T * (ss[3] + T * ss[4]))) + ss[5];
-            const double e = exp(hrt - sr);
+            const double e = fexp(hrt - sr, tb.exptab);
             const double ck = rho * y[k] * tb.invW[k];
             C[k] = ck;
             D[k] = e * ck;
@@ -585,7 +588,7 @@ struct GroupCell {
             const int r0 = a & 0xff, r1 = (a >> 8) & 0xff, r2 = (a >> 16) & 0xff, p0 = a >> 24;
             const int p1 = b & 0xff, p2 = (b >> 8) & 0xff, dnu = (int)((b >> 16) & 0xff) - 8;
             const double *rp = tb.rpar + 3 * j;
-            const double kf = exp(rp[0] + rp[1] * lnT - rp[2] * invT);
+            const double kf = fexp(rp[0] + rp[1] * lnT - rp[2] * invT, tb.exptab);
             // kr prod_p C_p = kf / Kc prod_p C_p = kf * G * B with
             // G = prod_r exp(-g_r) (P_atm/RT)^-dnu and B = prod_p exp(g_p) C_p
             const double c0 = C[r0], c1 = C[r1], c2 = C[r2];

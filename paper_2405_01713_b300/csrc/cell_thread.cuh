@@ -39,6 +39,7 @@ struct CoolingSmem {
     int n;
     double gamma_heat;
     const double *lnT, *lnLam, *slope;
+    const double *exptab;      // 2^(j/64), for fexp
 };
 
 // Heating-cooling of one gas cell (the Nyx split equation of Sec. 3.2,
@@ -72,8 +73,8 @@ struct CosmologyProblem {
             }
         }
         const double sl = tab->slope[lo];
-        const double lam = exp(tab->lnLam[lo] + sl * (lnT - x[lo]));
-        const double heat = tab->gamma_heat * exp(-0.7 * (lnT - LN1E4));
+        const double lam = fexp(tab->lnLam[lo] + sl * (lnT - x[lo]), tab->exptab);
+        const double heat = tab->gamma_heat * fexp(-0.7 * (lnT - LN1E4), tab->exptab);
         f = F + rho * (heat - lam);
         dfde = floor ? 0.0 : rho * (-0.7 * heat - sl * lam) * rcp(T);
     }

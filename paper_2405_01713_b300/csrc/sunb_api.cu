@@ -52,7 +52,7 @@ __device__ __forceinline__ void write_stats(int32_t *stats, int32_t *status, lon
 }
 
 struct CoolArgs {
-    const double *knots;   // [3 * n]: lnT, lnLam, slope (n-1 used)
+    const double *knots;   // [3 * n + EXP_TABLE_SIZE]: lnT, lnLam, slope (n-1 used), exp table
     int n;
     double gamma_heat;
 };
@@ -96,13 +96,14 @@ __device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned c
 __device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const CoolArgs &c)
 {
     double *d = reinterpret_cast<double *>(dst);
-    for (int i = threadIdx.x; i < 3 * c.n; i += blockDim.x) d[i] = c.knots[i];
+    for (int i = threadIdx.x; i < 3 * c.n + EXP_TABLE_SIZE; i += blockDim.x) d[i] = c.knots[i];
     CoolingSmem t;
     t.n = c.n;
     t.gamma_heat = c.gamma_heat;
     t.lnT = d;
     t.lnLam = d + c.n;
     t.slope = d + 2 * c.n;
+    t.exptab = d + 3 * c.n;
     return t;
 }
 
@@ -215,7 +216,7 @@ struct ThreadArgs {
 template <class Prob>
 __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 {
-    __shared__ __align__(16) double cool_s[3 * 256];
+    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();
@@ -273,7 +274,7 @@ __global__ void __launch_bounds__(128) mech_eval_kernel(const MechArgs a, const 
 template <class Prob>
 __global__ void thread_eval_kernel(const ThreadArgs a, const double *y, double *out, long long n, int mode)
 {
-    __shared__ __align__(16) double cool_s[3 * 256];
+    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();
@@ -590,6 +591,14 @@ __global__ void totals_kernel(const int32_t *stats, long long n, DevTotals *t)
 
 // ============================================================ host side
 
+// The right-hand sides' exponential on a device array, for its accuracy test.
+__device__ double g_exp_tab[EXP_TABLE_SIZE];
+__global__ void exp_check_kernel(const double *x, double *y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = fexp(x[i], g_exp_tab);
+}
+
 // One kernel launch of an outer step.
 struct LaunchSpec {
     void *func = nullptr;
@@ -668,6 +677,12 @@ static int fail(sunb_ctx *ctx, int code, const std::string &msg)
 
 static int align16(int x) { return (x + 15) & ~15; }
 
+// 2^(j/64), j < EXP_TABLE_SIZE, rounded to double (the table of fexp).
+static void fill_exp_table(double *t)
+{
+    for (int j = 0; j < EXP_TABLE_SIZE; ++j) t[j] = (double)exp2l((long double)j / (long double)EXP_TABLE_SIZE);
+}
+
 static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
 {
     const int K = m->n_species, M = m->n_reactions, N = K + 1;
@@ -719,6 +734,7 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     o.inc_j = take(4 * std::max(nnz, 1));
     o.inc_nuf = take(4 * std::max(nnz, 1));
     o.invWf = take(4 * K);
+    o.exptab = take(8 * EXP_TABLE_SIZE);
     o.bytes = off;
     std::vector<unsigned char> blob(off, 0);
     auto D = [&](int o_) { return reinterpret_cast<double *>(blob.data() + o_); };
@@ -754,6 +770,7 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     }
     I(o.inc_ptr)[K] = e;
     std::memcpy(blob.data() + o.ridx, ridx.data(), 4 * 2 * M);
+    fill_exp_table(D(o.exptab));
     ctx->off = o;
     ctx->blob.swap(blob);
     return SUNB_SUCCESS;
@@ -806,7 +823,7 @@ static void *pick_mech_kernel(int L, int precision, bool cosmo)
     return nullptr;
 }
 
-static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(8 * 3 * c->nknots) : 0; }
+static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(8 * (3 * c->nknots + EXP_TABLE_SIZE)) : 0; }
 
 // Shared memory of a mechanism CTA with c cells of L lanes: the tables, the
 // cooling table (mixed launches), the cells, one Newton-matrix scratch per
@@ -1169,7 +1186,8 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
             fail(ctx, SUNB_ILL_INPUT, "cooling table missing or with n_knots outside 2..256");
             return bail(SUNB_ILL_INPUT);
         }
-        std::vector<double> k(3 * t->n_knots, 0.0);
+        std::vector<double> k(3 * t->n_knots + EXP_TABLE_SIZE, 0.0);
+        fill_exp_table(k.data() + 3 * t->n_knots);
         for (int i = 0; i < t->n_knots; ++i) {
             k[i] = t->lnT[i];
             k[t->n_knots + i] = t->lnLam[i];
@@ -1404,6 +1422,34 @@ int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *d
     return lu_batched<float>(n, batch, dev_A, dev_piv, dev_b, dev_info, stream);
 }
 
+
+int sunb_exp_check(const double *dev_x, double *dev_y, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!dev_x || !dev_y))) {
+        g_create_error = "exp_check: need n >= 0 and device arrays";
+        return SUNB_ILL_INPUT;
+    }
+    if (n == 0) return SUNB_SUCCESS;
+    double tab[EXP_TABLE_SIZE];
+    fill_exp_table(tab);
+    cudaStream_t st = (cudaStream_t)stream;
+    if (cudaMemcpyToSymbolAsync(g_exp_tab, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+        g_create_error = "exp_check: table copy failed";
+        return SUNB_CUDA_ERROR;
+    }
+    const int grid = (int)std::min<long long>((n + 255) / 256, 148 * 8);
+    exp_check_kernel<<<grid, 256, 0, st>>>(dev_x, dev_y, (long long)n);
+    if (cudaGetLastError() != cudaSuccess) {
+        g_create_error = "exp_check: launch failed";
+        return SUNB_CUDA_ERROR;
+    }
+    // the host table must outlive the asynchronous copy
+    if (cudaStreamSynchronize(st) != cudaSuccess) {
+        g_create_error = "exp_check: kernel failed";
+        return SUNB_CUDA_ERROR;
+    }
+    return SUNB_SUCCESS;
+}
 
 int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final)
 {

@@ -11,6 +11,40 @@
 
 namespace sunb {
 
+// ---------------- exponential used by the right-hand sides ----------------
+// exp(x) by table-driven range reduction (P. T. P. Tang, "Table-driven
+// implementation of the exponential function in IEEE floating-point
+// arithmetic", ACM TOMS 15(2), 1989), with 64 table entries:
+//   x = (64 m + j) ln2/64 + r,  |r| <= ln2/128,
+//   exp(x) = 2^m * 2^(j/64) * (1 + p(r)),
+// p(r) the degree-5 Taylor polynomial of e^r - 1 (truncation below 4e-17
+// relative).  ln2/64 is split as C1 + C2 with C1 of 32 significant bits, so
+// that n C1 is exact; n is the nearest integer to 64 x/ln2, read from the
+// low word of x 64/ln2 + 1.5*2^52.  tab[j] = 2^(j/64) rounded to double
+// (EXP_TABLE_SIZE entries, filled by the host).  For |x| >= 704, where
+// 2^m would leave the normal range, and for NaN the library exp is used.
+// Accuracy: within 2 ulp of exp (checked against it by the GPU tests).
+constexpr int EXP_TABLE_SIZE = 64;   // the shifts below (>> 6, & 63) assume 64
+__device__ __forceinline__ double fexp(double x, const double *tab)
+{
+    if (!(fabs(x) < 704.0)) return exp(x);
+    const double shift = 6755399441055744.0;                 // 1.5 * 2^52
+    const double t = fma(x, 0x1.71547652b82fep+6, shift);    // 64 / ln 2
+    const int n = __double2loint(t);
+    const double nd = t - shift;
+    double r = fma(-nd, 0x1.62e42ff000000p-7, x);            // C1
+    r = fma(-nd, -0x1.718432a1b0e26p-41, r);                 // C2
+    double p = fma(r, 1.0 / 120.0, 1.0 / 24.0);
+    p = fma(r, p, 1.0 / 6.0);
+    p = fma(r, p, 0.5);
+    p = fma(r, p, 1.0);
+    p *= r;
+    const double tj = tab[n & (EXP_TABLE_SIZE - 1)];
+    const double v = fma(tj, p, tj);
+    return __hiloint2double(__double2hiint(v) + ((n >> 6) << 20), __double2loint(v));
+}
+
+
 constexpr int QMAX = 5;
 constexpr int NVEC = 12;            // per-cell vectors held by the controller
 

@@ -2,6 +2,8 @@
 right-hand side (step a5, Eq. chemODE / nyxODE), analytic Jacobian (a6,
 Table 1 approach 2A) and the batched pivoted LU (a7, Sec. 4.1.6), against
 the CPU oracle (complex-step Jacobian, plain LU)."""
+import math
+
 import numpy as np
 import pytest
 
@@ -151,3 +153,31 @@ def test_lu_rejects_bad_sizes():
     with pytest.raises(m.SunbError) as e:
         m.lu_solve_batched(A, b)
     assert e.value.code == m.ILL_INPUT
+
+
+def test_rhs_exponential_within_two_ulp_of_exp():
+    """The table-driven exponential of the right-hand sides against the
+    library exp: within 2 ulp over the range it handles itself, equal to it
+    outside (|x| >= 704, inf, NaN), and exact at 0."""
+    need_gpu()
+    m = sb()
+    g = torch.Generator(device="cpu").manual_seed(5)
+    parts = [
+        (torch.rand(2_000_000, generator=g, dtype=torch.float64) * 2 - 1) * 703.9,
+        (torch.rand(200_000, generator=g, dtype=torch.float64) * 2 - 1) * 1e-3,
+        # near the reduction boundaries (n + 1/2) ln2/64
+        (torch.arange(-20000, 20000, dtype=torch.float64) + 0.5) * (math.log(2) / 64),
+        torch.tensor([0.0, -0.0, 1.0, -1.0, 703.99, -703.99, 704.0, -704.0, 709.7, -745.2, -800.0,
+                      800.0, float("inf"), float("-inf"), 1e-300, -1e-300], dtype=torch.float64),
+    ]
+    x = torch.cat(parts).cuda()
+    y = m.exp_check(x)
+    ref = torch.exp(x)
+    assert torch.all(y[x == 0.0] == 1.0)
+    inside = x.abs() < 704.0
+    ulp = (torch.nextafter(ref, torch.full_like(ref, float("inf"))) - ref)[inside]
+    err = ((y - ref)[inside].abs() / ulp).max().item()
+    assert err <= 2.0, err
+    assert torch.equal(y[~inside], ref[~inside])
+    nan = m.exp_check(torch.tensor([float("nan")], dtype=torch.float64, device="cuda"))
+    assert torch.isnan(nan).all()
