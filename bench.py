@@ -225,9 +225,18 @@ def time_form(w, form, steps, warmup, flush):
     y = torch.empty_like(y0)
     p = torch.tensor(P, device="cuda")
     it.set_params(p)
-    def one_step():
+    kev = []        # events around the integrator launch alone (the dominant kernel)
+
+    def one_step(timed=False):
         y.copy_(y0)
+        if timed:
+            k0 = torch.cuda.Event(enable_timing=True)
+            k1 = torch.cuda.Event(enable_timing=True)
+            k0.record(stream)
         it.integrate(y, w["t0"], w["tout"])
+        if timed:
+            k1.record(stream)
+            kev.append((k0, k1))
         if adjoint:
             it.adjoint_replay(yrep)
             dL[:, :K] = 2 * (yrep[:, :K] - target)
@@ -243,10 +252,11 @@ def time_form(w, form, steps, warmup, flush):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        one_step()
+        one_step(timed=True)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+    kernel_ms = [a.elapsed_time(b) for a, b in kev]
     launches = it.launch_count - l0
     tot = it.totals()
     parts = None
@@ -254,7 +264,8 @@ def time_form(w, form, steps, warmup, flush):
         parts = split_totals(it.cell_stats(), w["n_cosmo"])
     mapping = it.mapping() if w["kind"] in ("mechanism", "mixed") else None
     it.close()
-    return dict(ms=times, launches=launches, totals=tot, mapping=mapping, C=C, parts=parts)
+    return dict(ms=times, kernel_ms=kernel_ms, launches=launches, totals=tot, mapping=mapping, C=C,
+                parts=parts)
 
 
 def time_e2e(w, form, steps, warmup):
@@ -403,9 +414,12 @@ def main():
         flops = work_model("mechanism", mech, t) + t["nst"] * (3 * per_setup + 12 * mech.n_reactions)
     else:
         flops = work_model(w["kind"], w.get("mech"), res["totals"])
-    achieved = flops / (ms / 1e3) / 1e12
+    # the integrator launch alone, timed on its stream (for the adjoint
+    # workload the step's three phases together)
+    kms = ms if w["name"] == "adjoint" else statistics.mean(res["kernel_ms"])
+    achieved = flops / (kms / 1e3) / 1e12
     roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
-            "frac": achieved / FP64_PEAK_DERIVED, "traffic": None,
+            "frac": achieved / FP64_PEAK_DERIVED, "traffic": None, "kernel_ms": kms,
             "peak_source": "derived: 148 SMs x 2032 MHz x 2 DFMA/clk/SM x 2 (FP64 pipe)"}
     if rank != 0:
         return

@@ -567,68 +567,88 @@ struct GroupCell {
         const double rts = RU * T * s;
         const double rho = P * rcp(rts);
         const double rrho = rts * invP;
-        for (int k = g.lane; k < K; k += L) {
-            const double *a = tb.cpc + 5 * k, *hh = tb.hc + 6 * k, *ss = tb.sc + 6 * k;
-            const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
-            const double hrt = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
-            const double sr = ss[0] * lnT + T * (ss[1] + T * (ss[2] + T * (ss[3] + T * ss[4]))) + ss[5];
-            const double e = fexp(hrt - sr, tb.exptab);
-            const double ck = rho * y[k] * tb.invW[k];
-            C[k] = ck;
-            D[k] = e * ck;
-            egi[k] = rcp(e);
-            hRT[k] = hrt;
-            cpR[k] = cp;
+        {
+            // distinct shared-memory arrays: restrict lets loads of the next
+            // species move above this species' stores
+            const double *__restrict__ yr = y;
+            const double *__restrict__ cpc = tb.cpc, *__restrict__ hc = tb.hc, *__restrict__ sc = tb.sc;
+            const double *__restrict__ iW = tb.invW, *__restrict__ xt = tb.exptab;
+            double *__restrict__ Cw = C, *__restrict__ Dw = D, *__restrict__ Ew = egi;
+            double *__restrict__ Hw = hRT, *__restrict__ Pw = cpR;
+            for (int k = g.lane; k < K; k += L) {
+                const double *a = cpc + 5 * k, *hh = hc + 6 * k, *ss = sc + 6 * k;
+                const double cp = a[0] + T * (a[1] + T * (a[2] + T * (a[3] + T * a[4])));
+                const double hrt = hh[0] + T * (hh[1] + T * (hh[2] + T * (hh[3] + T * hh[4]))) + hh[5] * invT;
+                const double sr = ss[0] * lnT + T * (ss[1] + T * (ss[2] + T * (ss[3] + T * ss[4]))) + ss[5];
+                const double e = fexp(hrt - sr, xt);
+                const double ck = rho * yr[k] * iW[k];
+                Cw[k] = ck;
+                Dw[k] = e * ck;
+                Ew[k] = rcp(e);
+                Hw[k] = hrt;
+                Pw[k] = cp;
+            }
         }
         g.sync();
         const double rtp = RU * T * (1.0 / PATM), irtp = rcp(rtp);
         const double pw[5] = {irtp * irtp, irtp, 1.0, rtp, rtp * rtp};
+        const double *__restrict__ Cr = C, *__restrict__ Dr = D, *__restrict__ Er = egi, *__restrict__ Hr = hRT;
+        const double *__restrict__ rpar = tb.rpar, *__restrict__ xt = tb.exptab;
+        const uint32_t *__restrict__ ridx = tb.ridx;
+        double *__restrict__ qw = q, *__restrict__ dTw = dqdT, *__restrict__ uw = uq;
+        MT *__restrict__ dqw = dq;
         for (int j = g.lane; j < M; j += L) {
-            const uint32_t a = tb.ridx[2 * j], b = tb.ridx[2 * j + 1];
+            const uint32_t a = ridx[2 * j], b = ridx[2 * j + 1];
             const int r0 = a & 0xff, r1 = (a >> 8) & 0xff, r2 = (a >> 16) & 0xff, p0 = a >> 24;
             const int p1 = b & 0xff, p2 = (b >> 8) & 0xff, dnu = (int)((b >> 16) & 0xff) - 8;
-            const double *rp = tb.rpar + 3 * j;
-            const double kf = fexp(rp[0] + rp[1] * lnT - rp[2] * invT, tb.exptab);
+            const double *rp = rpar + 3 * j;
+            const double kf = fexp(rp[0] + rp[1] * lnT - rp[2] * invT, xt);
             // kr prod_p C_p = kf / Kc prod_p C_p = kf * G * B with
             // G = prod_r exp(-g_r) (P_atm/RT)^-dnu and B = prod_p exp(g_p) C_p
-            const double c0 = C[r0], c1 = C[r1], c2 = C[r2];
+            const double c0 = Cr[r0], c1 = Cr[r1], c2 = Cr[r2];
             const double A = c0 * c1 * c2;
-            const double G = (egi[r0] * egi[r1] * egi[r2]) * pw[dnu + 2];
-            const double B = D[p0] * D[p1] * D[p2];
-            q[j] = kf * (A - G * B);
+            const double G = (Er[r0] * Er[r1] * Er[r2]) * pw[dnu + 2];
+            const double B = Dr[p0] * Dr[p1] * Dr[p2];
+            qw[j] = kf * (A - G * B);
             if (jac) {
-                MT *dj = dq + 6 * j;
+                MT *dj = dqw + 6 * j;
                 const double rkf = kf * G;                 // kr = rkf prod_p exp(g_p)
                 const double fwd = kf * A, rev = rkf * B;
                 const double gkf = gamma * kf, grk = gamma * rkf;
-                const double D0 = D[p0], D1 = D[p1], D2 = D[p2];
+                const double D0 = Dr[p0], D1 = Dr[p1], D2 = Dr[p2];
                 dj[0] = (MT)(gkf * (c1 * c2));
                 dj[1] = (MT)(gkf * (c0 * c2));
                 dj[2] = (MT)(gkf * (c0 * c1));
                 // gamma kr prod_{p != i} C_p = gamma rkf exp(g_i) prod_{p != i} D_p
-                dj[3] = (MT)(-grk * rcp(egi[p0]) * (D1 * D2));
-                dj[4] = (MT)(-grk * rcp(egi[p1]) * (D0 * D2));
-                dj[5] = (MT)(-grk * rcp(egi[p2]) * (D0 * D1));
+                dj[3] = (MT)(-grk * rcp(Er[p0]) * (D1 * D2));
+                dj[4] = (MT)(-grk * rcp(Er[p1]) * (D0 * D2));
+                dj[5] = (MT)(-grk * rcp(Er[p2]) * (D0 * D1));
                 const double af = rp[1] + rp[2] * invT;
-                const double dH = (hRT[p0] + hRT[p1] + hRT[p2]) - (hRT[r0] + hRT[r1] + hRT[r2]);
-                dqdT[j] = gamma * invT * (af * fwd - (af - dH + (double)dnu) * rev);
+                const double dH = (Hr[p0] + Hr[p1] + Hr[p2]) - (Hr[r0] + Hr[r1] + Hr[r2]);
+                dTw[j] = gamma * invT * (af * fwd - (af - dH + (double)dnu) * rev);
                 // sum_m C_m dq_j/dC_m = n_r fwd - n_p rev (each product term is
                 // homogeneous in C): formed in FP64 here, because summing the
                 // large, nearly cancelling row entries instead loses it in FP32
                 const int nr = (int)(b >> 24), np = nr + dnu;
-                uq[j] = gamma * ((double)nr * fwd - (double)np * rev);
+                uw[j] = gamma * ((double)nr * fwd - (double)np * rev);
             }
         }
         g.sync();
         double hw = 0.0, cpm = 0.0;
-        for (int k = g.lane; k < K; k += L) {
-            double wd = 0.0;
-            const int e1 = tb.inc_ptr[k + 1];
-            for (int e = tb.inc_ptr[k]; e < e1; ++e) wd += tb.inc_nu[e] * q[tb.inc_j[e]];
-            f[k] = wd * tb.W[k] * rrho;
-            hw += hRT[k] * wd;
-            cpm += y[k] * cpR[k] * tb.invW[k];
-            if (jac) wdot[k] = wd;
+        {
+            const double *__restrict__ qr = q, *__restrict__ nu = tb.inc_nu, *__restrict__ Hr2 = hRT;
+            const double *__restrict__ Pr = cpR, *__restrict__ yr = y, *__restrict__ Wr = tb.W, *__restrict__ iW = tb.invW;
+            const int32_t *__restrict__ ip = tb.inc_ptr, *__restrict__ ij = tb.inc_j;
+            double *__restrict__ fw = f, *__restrict__ ww = wdot;
+            for (int k = g.lane; k < K; k += L) {
+                double wd = 0.0;
+                const int e1 = ip[k + 1];
+                for (int e = ip[k]; e < e1; ++e) wd += nu[e] * qr[ij[e]];
+                fw[k] = wd * Wr[k] * rrho;
+                hw += Hr2[k] * wd;
+                cpm += yr[k] * Pr[k] * iW[k];
+                if (jac) ww[k] = wd;
+            }
         }
         hw = g.sum(hw);
         cpm = g.sum(cpm);

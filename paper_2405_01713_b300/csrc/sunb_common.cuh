@@ -25,7 +25,7 @@ namespace sunb {
 // 2^m would leave the normal range, and for NaN the library exp is used.
 // Accuracy: within 2 ulp of exp (checked against it by the GPU tests).
 constexpr int EXP_TABLE_SIZE = 64;   // the shifts below (>> 6, & 63) assume 64
-__device__ __forceinline__ double fexp(double x, const double *tab)
+__device__ __forceinline__ double fexp(double x, const double *__restrict__ tab)
 {
     if (!(fabs(x) < 704.0)) return exp(x);
     const double shift = 6755399441055744.0;                 // 1.5 * 2^52
