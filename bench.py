@@ -59,6 +59,15 @@ def jac_extra_flops(mech):
     return M * 22 + nnz * 14 + 2 * K * K + 2 * K * K + 4 * K * K + 10 * K + N * N
 
 
+# DRAM bytes (read + write) per cell of one integrator launch, from one ncu
+# capture of a smaller batch of the same kernel and launch shape, scaled by
+# cells (traffic is per cell: y in and out, parameters, counters):
+#   ncu --set full --clock-control none -k regex:mech_kernel -c 1 python bench.py
+#       --workload mech22 --cells 7168 --lanes 8 --steps 1 --warmup 1 --no-plain --no-cpu --no-e2e
+# -> 1.70 MB + 2.21 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md).
+TRAFFIC_BYTES_PER_CELL = {"mech22": 545.0}
+
+
 def work_model(kind, mech, tot):
     """Algorithmic FP64 flops of one launch from the per-cell counters:
     f evaluations, Newton-matrix builds (J + LU (2/3)N^3), Newton iterations
@@ -418,8 +427,11 @@ def main():
     # workload the step's three phases together)
     kms = ms if w["name"] == "adjoint" else statistics.mean(res["kernel_ms"])
     achieved = flops / (kms / 1e3) / 1e12
+    traffic = None
+    if w["name"] in TRAFFIC_BYTES_PER_CELL:
+        traffic = TRAFFIC_BYTES_PER_CELL[w["name"]] * res["C"]
     roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
-            "frac": achieved / FP64_PEAK_DERIVED, "traffic": None, "kernel_ms": kms,
+            "frac": achieved / FP64_PEAK_DERIVED, "traffic": traffic, "kernel_ms": kms,
             "peak_source": "derived: 148 SMs x 2032 MHz x 2 DFMA/clk/SM x 2 (FP64 pipe)"}
     if rank != 0:
         return
