@@ -337,8 +337,8 @@ __global__ void __launch_bounds__(128) lu_batched_kernel(int n, long long batch,
 // ---------------------------------------------------------------- adjoint
 // Discrete adjoint of the recorded forward map (one warp per cell, FP64).
 // Replay: recompute the step history from the tape header (y0, h0) with each
-// corrector solved by full Newton (fresh analytic Jacobian per iteration) to
-// rounding level, overwriting the tape's states with these exact ones.
+// corrector solved to rounding level (Newton with the analytic Jacobian at
+// the recorded state), overwriting the tape's states with these exact ones.
 // Reverse: lam (the adjoint of the Nordsieck array) is carried back through
 // each step's update, corrector (mu = (I - gamma J(y_n))^{-T} lam_Delta),
 // prediction and column map, accumulating gamma (df/dtheta)^T mu for
@@ -431,9 +431,14 @@ __global__ void __launch_bounds__(128) adjoint_replay_kernel(const AdjArgs a)
             }
             c.g.sync();
             c.predict(q);
-            for (int it = 0; it < 12; ++it) {             // full Newton, exact J
-                c.eval(V_Y, V_F, gamma, true);
-                if (!c.factor()) break;
+            // Newton to rounding level with the matrix at the recorded state
+            // (already within the forward Newton tolerance of the exact
+            // corrector, so the iteration contracts by orders of magnitude
+            // per step); f is re-evaluated every iteration
+            c.eval(V_Y, V_F, gamma, true);
+            const int have = c.factor();
+            for (int it = 0; it < 20 && have; ++it) {
+                if (it > 0) c.rhs(V_Y, V_F);
                 for (int i = c.g.lane; i < N; i += L)
                     d[i] = -(y[i] - gamma * f[i] - (z0[i] - il1 * c.vec[c.NP + i]));
                 c.g.sync();
