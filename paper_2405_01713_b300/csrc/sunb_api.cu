@@ -210,9 +210,14 @@ struct ThreadArgs {
     Controls ctl;
     double atol[3];
     CoolArgs cool;
+    int spread_lanes;   // > 0: one wave, lanes [0, spread_lanes) of every warp take a cell each
 };
 
-// Thread-per-cell kernel for Robertson and cosmology batches.
+// Thread-per-cell kernel for Robertson and cosmology batches.  Large batches
+// take cells from the device queue; a batch that fits in one wave
+// (spread_lanes > 0) is spread over all SMs and warps instead, cell
+// b + grid (w + W l) for lane l < spread_lanes of warp w of CTA b, so that
+// few cells do not crowd a few SMs.
 template <class Prob>
 __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 {
@@ -224,9 +229,17 @@ __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
     if constexpr (Prob::N == 1) tc.prob.tab = &cool;
 #pragma unroll
     for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
+    bool taken = false;
     run_cells(
         tc, a.ctl, launched_warp_mask(),
         [&]() -> long long {
+            if (a.spread_lanes > 0) {
+                const int l = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+                if (taken || l >= a.spread_lanes) return -1;
+                taken = true;
+                const long long cell = blockIdx.x + (long long)gridDim.x * (w + (long long)W * l);
+                return cell < a.n ? cell : -1;
+            }
             const long long cell = grab_thread(a.queue);
             return cell < a.n ? cell : -1;
         },
@@ -1092,17 +1105,32 @@ static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
 }
 
 // Thread-per-cell launch: 256 threads per CTA, as many CTAs as stay resident.
-static int thread_spec(sunb_ctx *ctx, const ThreadArgs &a, bool robertson, LaunchSpec &sp)
+static int thread_spec(sunb_ctx *ctx, const ThreadArgs &a, bool robertson, LaunchSpec &sp,
+                       bool may_spread = true)
 {
     sp.thread = true;
     sp.ta = a;
     sp.func = robertson ? (void *)thread_kernel<RobertsonProblem> : (void *)thread_kernel<CosmologyProblem>;
+    sp.smem = 0;
+    // A batch of at most 256 cells per SM runs as one wave spread over every
+    // SM, at most 8 warps of about 2 cells each per SM: 1024 Robertson cells
+    // took 22.1 ms on 4 SMs from the queue, 10.0 ms as 1 warp of 7 cells per
+    // SM, 8.7 ms as 7 warps of 1 cell and 7.8 ms as 4 warps of 2 (B300).
+    constexpr int SPREAD_LANES = 2, SPREAD_WARPS = 8;
+    const long long per_sm = (a.n + ctx->num_sms - 1) / ctx->num_sms;
+    if (may_spread && per_sm <= (long long)SPREAD_WARPS * 32) {
+        const int W = (int)std::min<long long>(SPREAD_WARPS, (per_sm + SPREAD_LANES - 1) / SPREAD_LANES);
+        sp.ta.spread_lanes = (int)((per_sm + W - 1) / W);
+        sp.grid = dim3((unsigned)ctx->num_sms);
+        sp.block = dim3(32 * std::max(1, W));
+        return SUNB_SUCCESS;
+    }
+    sp.ta.spread_lanes = 0;
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, sp.func, 256, 0));
     const long long want = (a.n + 255) / 256;
     sp.grid = dim3((unsigned)std::max(1LL, std::min<long long>(want, (long long)ctx->num_sms * std::max(1, occ))));
     sp.block = dim3(256);
-    sp.smem = 0;
     return SUNB_SUCCESS;
 }
 
@@ -1132,7 +1160,9 @@ static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
         ta.n = ctx->Cc;
         ta.queue = ctx->d_queue + 1;
         ta.atol[0] = ctx->atol[ctx->off.N];
-        const int rc = thread_spec(ctx, ta, false, sp[1]);
+        // the queue, never the spread: the mechanism kernel's tail has
+        // taken cells from the same counter
+        const int rc = thread_spec(ctx, ta, false, sp[1], false);
         if (rc != SUNB_SUCCESS) return rc;
         n = 2;
     }
