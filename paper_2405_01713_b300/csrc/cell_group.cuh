@@ -243,8 +243,9 @@ struct GroupCell {
     int32_t *perm;        // [N] row permutation of the factorisation
     MT *xs;               // [N] solve scratch
     MT *dinv;             // [N] reciprocal pivots
-    double *C, *D, *egi, *hRT, *cpR, *wdot, *u, *wT;    // species scratch ([K+1] for the first four);
+    double *C, *D, *egi, *hRT, *cpR;                    // species scratch ([K+1] for the first four);
                                                         // D_k = exp(g_k) C_k, egi_k = exp(-g_k)
+    double *wdot, *u, *wT;                              // [K] each, Newton-matrix builds only
     double *q;                                          // [M]
     MT *dq;                                             // [6M] gamma dq_j/dC at each position
     double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
@@ -269,7 +270,7 @@ struct GroupCell {
         dinv = xs + N;
         double *sp = reinterpret_cast<double *>(base + lay.sp);
         C = sp; D = C + (K + 1); egi = D + (K + 1); hRT = egi + (K + 1);
-        cpR = hRT + (K + 1); wdot = cpR + K; u = wdot + K; wT = u + K;
+        cpR = hRT + (K + 1);
         q = reinterpret_cast<double *>(base + lay.rq);
         if (lay.dq >= 0) set_jac_scratch(base + lay.dq, nullptr);
         if (lay.pm >= 0) {
@@ -285,8 +286,9 @@ struct GroupCell {
         g.sync();
     }
 
-    // Newton-matrix scratch: dq [6M] in MT, then dqdT and uq [M] in FP64
-    // (jac_scratch_bytes).  With a lock, the groups of a warp share one
+    // Newton-matrix scratch: dq [6M] in MT, then dqdT and uq [M] and wdot,
+    // u, wT [K] in FP64 (jac_scratch_bytes).  With a lock, the groups of a
+    // warp share one
     // scratch: a group takes it before a set-up (acquire_setup) and gives
     // it back once its matrix is assembled, within one superstep, so no
     // group ever waits for it.
@@ -295,6 +297,9 @@ struct GroupCell {
         dq = reinterpret_cast<MT *>(p);
         dqdT = reinterpret_cast<double *>(p + ((6 * M * (int)sizeof(MT) + 15) & ~15));
         uq = dqdT + M;
+        wdot = uq + M;
+        u = wdot + K;
+        wT = u + K;
         jac_lock = lock;
     }
     __device__ __forceinline__ bool acquire_setup()

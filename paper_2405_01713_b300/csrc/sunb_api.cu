@@ -795,8 +795,8 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
 }
 
 // Bytes of one Newton-matrix scratch: dq [6M] in the matrix type, then
-// dqdT and uq [M] in FP64 (GroupCell::set_jac_scratch).
-static int jac_scratch_bytes(int M, int mt) { return align16(mt * 6 * M) + 16 * M; }
+// dqdT and uq [M] and wdot, u, wT [K] in FP64 (GroupCell::set_jac_scratch).
+static int jac_scratch_bytes(int M, int K, int mt) { return align16(mt * 6 * M) + 16 * M + 24 * K; }
 
 static CellLayout make_layout(int N, int K, int M, int mt, bool dq_in_cell = true, bool with_pm = true)
 {
@@ -808,9 +808,9 @@ static CellLayout make_layout(int N, int K, int M, int mt, bool dq_in_cell = tru
     l.mat = take(mt * N * N);
     l.perm = take(4 * N);
     l.xs = take(mt * 2 * N);
-    l.sp = take(8 * (4 * (K + 1) + 4 * K));
+    l.sp = take(8 * (4 * (K + 1) + K));
     l.rq = take(8 * M);
-    l.dq = dq_in_cell ? take(jac_scratch_bytes(M, mt)) : -1;
+    l.dq = dq_in_cell ? take(jac_scratch_bytes(M, K, mt)) : -1;
     l.pm = with_pm ? take(8 * (36 + K + 1)) : -1;   // adjoint column map and scratch
     l.bytes = off;
     return l;
@@ -855,7 +855,7 @@ static MechSmem mech_smem(const sunb_ctx *ctx, int c, int L)
     const int mt = ctx->precision == SUNB_MIXED32 ? 4 : 8;
     const int warps = (c * L + 31) / 32;
     m.cells_off = ctx->off.bytes + (ctx->kind == SUNB_MIXED ? cool_bytes(ctx) : 0);
-    m.dq_bytes = jac_scratch_bytes(ctx->off.M, mt);
+    m.dq_bytes = jac_scratch_bytes(ctx->off.M, ctx->off.K, mt);
     m.dq_off = m.cells_off + c * ctx->lay.bytes;
     m.lock_off = m.dq_off + warps * m.dq_bytes;
     m.bytes = m.lock_off + align16(4 * warps);
