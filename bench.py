@@ -157,24 +157,42 @@ class ClockSampler:
 
 
 # --------------------------------------------------------------------- workloads
-def make_workload(name, cells=None):
+def make_workload(name, cells=None, shard=0):
     """The named workload at full size, or its first ``cells`` cells (for
-    small profiling cases; prefix-compatible with the full batch)."""
-    kw = {} if cells is None else {"n_cells": cells}
-    if name == "mech22":
-        return synth.workloads.mech22(**kw)
-    if name == "mech54":
-        return synth.workloads.mech54(**kw)
-    if name == "robertson":
-        return synth.workloads.robertson(**kw)
+    small profiling cases; prefix-compatible with the full batch).  Rank
+    ``shard`` of a multi-GPU run takes the next full-size batch of the same
+    cell sequence (weak scaling: every rank integrates its own cells)."""
     if name == "mixed":
-        return synth.workloads.mixed() if cells is None else \
-            synth.workloads.mixed(n_cosmo=cells * 256, n_mech=cells)
-    if name == "cosmology":
-        return synth.workloads.cosmology(2 ** 24 if cells is None else cells)
-    if name == "adjoint":
-        return synth.workloads.adjoint(**kw)
-    raise ValueError(name)
+        n_cosmo, n_mech = (2 ** 24, 2 ** 16) if cells is None else (cells * 256, cells)
+        return synth.workloads.mixed(n_cosmo=n_cosmo, n_mech=n_mech, shard=shard)
+    full = {"mech22": 2 ** 18, "mech54": 2 ** 20, "robertson": 1024, "cosmology": 2 ** 24,
+            "adjoint": 2 ** 16}[name]
+    n = full if cells is None else cells
+    return getattr(synth.workloads, name)(n, first_cell=shard_cells(n, shard))
+
+
+def shard_cells(n_cells, rank):
+    """First cell of rank ``rank``'s shard (weak scaling)."""
+    return rank * n_cells
+
+
+def max_over_ranks(x, world):
+    """The largest x over the ranks of the default process group (the
+    slowest rank's time); x itself for a single rank."""
+    if world <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([float(x)], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
 
 
 LANES_OVERRIDE = 0
@@ -207,7 +225,7 @@ def make_integrator(w, form):
 ADJOINT_CAP = 1536   # tape capacity (accepted steps per cell) of the adjoint workload
 
 
-def time_form(w, form, steps, warmup, flush):
+def time_form(w, form, steps, warmup, flush, world=1):
     """Device-resident timing of one form: per step, copy y0 -> y and
     integrate (for the adjoint workload: integrate with tapes, replay, and
     the reverse sweep to the [M, 2] gradient of the squared-error loss),
@@ -254,6 +272,7 @@ def time_form(w, form, steps, warmup, flush):
     for _ in range(warmup):
         one_step()
     torch.cuda.synchronize()
+    barrier(world)
     l0 = it.launch_count
     times = []
     for _ in range(steps):
@@ -265,6 +284,8 @@ def time_form(w, form, steps, warmup, flush):
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1))
+    torch.cuda.synchronize()
+    barrier(world)
     kernel_ms = [a.elapsed_time(b) for a, b in kev]
     launches = it.launch_count - l0
     tot = it.totals()
@@ -360,7 +381,7 @@ def main():
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
-    w = make_workload(args.workload, args.cells)
+    w = make_workload(args.workload, args.cells, shard=rank)
     w.setdefault("name", args.workload)
     workload_name = {"mech22": "mech22: 21 species + T, 84 reactions, 2^18 cells, dt 1e-6 s",
                      "mech54": "mech54: 53 species + T, 270 reactions, 2^20 cells, dt 1e-6 s",
@@ -398,16 +419,11 @@ def main():
     clocks = ClockSampler(int(os.environ.get("LOCAL_RANK", "0")))
     res_plain = None
     if not args.no_plain and w["kind"] in ("mechanism", "mixed") and w["name"] != "adjoint":
-        res_plain = time_form(w, "plain", args.steps, args.warmup, flush)
+        res_plain = time_form(w, "plain", args.steps, args.warmup, flush, world)
     clocks.start()
-    res = time_form(w, "chosen", args.steps, args.warmup, flush)
+    res = time_form(w, "chosen", args.steps, args.warmup, flush, world)
     clk = clocks.stop()
-    ms = statistics.mean(res["ms"])
-    if world > 1:
-        import torch.distributed as dist
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
+    ms = max_over_ranks(statistics.mean(res["ms"]), world)
     value = world * res["C"] / (ms / 1e3)
 
     # the counters describe the last launch (they are reset by every call)

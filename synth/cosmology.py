@@ -41,11 +41,12 @@ def make_cooling_table(seed):
     return CoolingTable(lnT, lnLam, GAMMA_HEAT)
 
 
-def cosmology_cells(n_cells, seed):
+def cosmology_cells(n_cells, seed, first=0):
     """Initial energies [C,1] (T0 log-uniform in [1e2, 1e8] K) and per-cell
-    parameters [C,2] = (rho, F), rho log-uniform over [1e-3, 1e3], F = 0."""
-    e0 = Stream(seed, 42).log_uniform(n_cells, 1e2, 1e8).reshape(n_cells, 1)
-    rho = Stream(seed, 43).log_uniform(n_cells, 1e-3, 1e3)
+    parameters [C,2] = (rho, F), rho log-uniform over [1e-3, 1e3], F = 0, of
+    cells first .. first+C-1."""
+    e0 = Stream(seed, 42).skip(first).log_uniform(n_cells, 1e2, 1e8).reshape(n_cells, 1)
+    rho = Stream(seed, 43).skip(first).log_uniform(n_cells, 1e-3, 1e3)
     params = np.zeros((n_cells, 2))
     params[:, 0] = rho
     return e0, params

@@ -116,8 +116,9 @@ def make_mechanism(n_species, n_reactions, seed):
     return Mechanism(K, M, W, nasa, react, prod, lnA, beta, Ea, comp)
 
 
-def mechanism_cells(mech, n_cells, seed, T_range=(800.0, 2500.0), alpha=0.5):
-    """Initial states [C, K+1] (mass fractions then T) and per-cell pressure.
+def mechanism_cells(mech, n_cells, seed, T_range=(800.0, 2500.0), alpha=0.5, first=0):
+    """Initial states [C, K+1] (mass fractions then T) and per-cell pressure
+    of cells first .. first+C-1 of the seeded sequence.
 
     T0 is uniform in ``T_range``; mass fractions are Dirichlet(alpha), drawn as
     normalised Gamma(1/2) variates (Z**2/2 for a standard normal Z) when
@@ -126,8 +127,8 @@ def mechanism_cells(mech, n_cells, seed, T_range=(800.0, 2500.0), alpha=0.5):
     if alpha != 0.5:
         raise ValueError("only Dirichlet(1/2) is implemented")
     K = mech.n_species
-    s_t = Stream(seed, 21)
-    s_y = Stream(seed, 22)
+    s_t = Stream(seed, 21).skip(first)
+    s_y = Stream(seed, 22).skip(2 * K * first)
     T0 = s_t.uniform(n_cells, T_range[0], T_range[1])
     z = s_y.normal(n_cells * K).reshape(n_cells, K)
     g = 0.5 * z * z
@@ -139,9 +140,10 @@ def mechanism_cells(mech, n_cells, seed, T_range=(800.0, 2500.0), alpha=0.5):
     return y0, P
 
 
-def dirichlet_targets(n_cells, K, seed):
-    """Seeded target mass fractions (Dirichlet(1/2)) for the adjoint loss."""
-    z = Stream(seed, 31).normal(n_cells * K).reshape(n_cells, K)
+def dirichlet_targets(n_cells, K, seed, first=0):
+    """Seeded target mass fractions (Dirichlet(1/2)) for the adjoint loss,
+    cells first .. first+C-1."""
+    z = Stream(seed, 31).skip(2 * K * first).normal(n_cells * K).reshape(n_cells, K)
     g = 0.5 * z * z
     return g / g.sum(axis=1, keepdims=True)
 

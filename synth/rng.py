@@ -38,6 +38,12 @@ class Stream:
             self._base = _mix(s ^ np.uint64(0xD1B54A32D192ED03))
         self._next = 0
 
+    def skip(self, n):
+        """Advance past n draws (the stream of a batch that starts at a later
+        cell); returns self."""
+        self._next += int(n)
+        return self
+
     def u64(self, n):
         i = np.arange(self._next, self._next + n, dtype=np.uint64)
         self._next += n

@@ -10,8 +10,8 @@ from .rng import Stream
 K_NOMINAL = np.array([0.04, 3.0e7, 1.0e4])
 
 
-def robertson_cells(n_cells, seed):
-    s = Stream(seed, 1)
+def robertson_cells(n_cells, seed, first=0):
+    s = Stream(seed, 1).skip(3 * first)
     f = s.uniform(n_cells * 3, 0.9, 1.1).reshape(n_cells, 3)
     k = f * K_NOMINAL
     y0 = np.zeros((n_cells, 3))

@@ -14,7 +14,8 @@ adjoint                mech22 mechanism, 2**16 cells, dt 1e-5 s, targets seed 5
 
 ``n_cells`` may be given to draw a prefix-compatible smaller batch: cell i of a
 small batch equals cell i of the full batch, so parity samples taken at full
-size can be recomputed one by one.
+size can be recomputed one by one.  ``first_cell`` starts the batch at a later
+cell of the same sequence (the shard of one rank of a multi-GPU run).
 """
 import functools
 
@@ -41,52 +42,53 @@ def cooling_table():
     return make_cooling_table(seed=4)
 
 
-def robertson(n_cells=1024):
-    y0, k = robertson_cells(n_cells, seed=1)
+def robertson(n_cells=1024, first_cell=0):
+    y0, k = robertson_cells(n_cells, seed=1, first=first_cell)
     return dict(name="robertson", kind="robertson", n_cells=n_cells, n_vars=3,
                 y0=y0, params=k, t0=0.0, tout=1.0e5, rtol=RTOL, atol=ATOL)
 
 
-def mech22(n_cells=2 ** 18):
+def mech22(n_cells=2 ** 18, first_cell=0):
     mech = mech22_mechanism()
-    y0, P = mechanism_cells(mech, n_cells, seed=2)
+    y0, P = mechanism_cells(mech, n_cells, seed=2, first=first_cell)
     return dict(name="mech22", kind="mechanism", mech=mech, n_cells=n_cells,
                 n_vars=mech.n_vars, y0=y0, params=P, t0=0.0, tout=1.0e-6,
                 rtol=RTOL, atol=ATOL)
 
 
-def mech54(n_cells=2 ** 20):
+def mech54(n_cells=2 ** 20, first_cell=0):
     mech = mech54_mechanism()
-    y0, P = mechanism_cells(mech, n_cells, seed=3)
+    y0, P = mechanism_cells(mech, n_cells, seed=3, first=first_cell)
     return dict(name="mech54", kind="mechanism", mech=mech, n_cells=n_cells,
                 n_vars=mech.n_vars, y0=y0, params=P, t0=0.0, tout=1.0e-6,
                 rtol=RTOL, atol=ATOL)
 
 
-def mixed(n_cosmo=2 ** 24, n_mech=2 ** 16):
+def mixed(n_cosmo=2 ** 24, n_mech=2 ** 16, shard=0):
     """Cosmology cells plus mech22-type cells integrated over one outer step
-    of 1e-6 s (cosmology cells first in the state and parameter arrays)."""
+    of 1e-6 s (cosmology cells first in the state and parameter arrays);
+    shard s holds cosmology cells s*n_cosmo.. and mechanism cells s*n_mech..."""
     table = cooling_table()
-    e0, cp = cosmology_cells(n_cosmo, seed=4)
+    e0, cp = cosmology_cells(n_cosmo, seed=4, first=shard * n_cosmo)
     mech = mech22_mechanism()
-    y0, P = mechanism_cells(mech, n_mech, seed=44)
+    y0, P = mechanism_cells(mech, n_mech, seed=44, first=shard * n_mech)
     return dict(name="mixed", kind="mixed", table=table, mech=mech,
                 n_cosmo=n_cosmo, n_mech=n_mech, e0=e0, cosmo_params=cp,
                 y0_mech=y0, mech_params=P, t0=0.0, tout=1.0e-6, rtol=RTOL, atol=ATOL)
 
 
-def cosmology(n_cells):
+def cosmology(n_cells, first_cell=0):
     table = cooling_table()
-    e0, cp = cosmology_cells(n_cells, seed=4)
+    e0, cp = cosmology_cells(n_cells, seed=4, first=first_cell)
     return dict(name="cosmology", kind="cosmology", table=table, n_cells=n_cells,
                 n_vars=1, y0=e0, params=cp, t0=0.0, tout=1.0e-6, rtol=RTOL,
                 atol=ATOL)
 
 
-def adjoint(n_cells=2 ** 16):
+def adjoint(n_cells=2 ** 16, first_cell=0):
     mech = mech22_mechanism()
-    y0, P = mechanism_cells(mech, n_cells, seed=5)
-    target = dirichlet_targets(n_cells, mech.n_species, seed=5)
+    y0, P = mechanism_cells(mech, n_cells, seed=5, first=first_cell)
+    target = dirichlet_targets(n_cells, mech.n_species, seed=5, first=first_cell)
     return dict(name="adjoint", kind="mechanism", mech=mech, n_cells=n_cells,
                 n_vars=mech.n_vars, y0=y0, params=P, t0=0.0, tout=1.0e-5,
                 rtol=RTOL, atol=ATOL, target=target)
