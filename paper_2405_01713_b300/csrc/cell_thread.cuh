@@ -31,6 +31,7 @@ struct RobertsonProblem {
         J[1][0] = k1;   J[1][1] = -k3 * y[2] - 2.0 * k2 * y[1];  J[1][2] = -k3 * y[1];
         J[2][0] = 0.0;  J[2][1] = 2.0 * k2 * y[1];               J[2][2] = 0.0;
     }
+    static constexpr bool kFusedJac = false;   // J costs extra work: only at set-ups
 };
 
 // Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
@@ -87,6 +88,12 @@ struct CosmologyProblem {
     {
         double f;
         eval(y[0], f, J[0][0]);
+    }
+    // f and df/de come from one evaluation
+    static constexpr bool kFusedJac = true;
+    __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
+    {
+        eval(y[0], f[0], J[0][0]);
     }
 };
 
@@ -273,19 +280,25 @@ struct ThreadCell {
     // the Newton matrix at y, factored (0: singular)
     __device__ __forceinline__ int newton_f(bool setup, double gamma)
     {
-        if (setup) return rhs_setup(V_Y, V_F, gamma);
-        rhs(V_Y, V_F);
-        return 1;
-    }
-    // f(z0) into slot fo, J at z0, M = I - gamma J, in-register LU with row
-    // partial pivoting (first index of largest magnitude).  Pivots are kept
-    // as an explicit permutation applied in solve().
-    int perm[N];
-    __device__ __forceinline__ int rhs_setup(int a, int fo, double gamma)
-    {
-        prob.rhs(v[a], v[fo]);
+        // where J comes with f (Prob::kFusedJac), one evaluation serves both,
+        // so that cells of a warp that set up and cells that do not share it
         double J[N][N];
-        prob.jac(v[a], J);
+        if constexpr (Prob::kFusedJac) {
+            prob.rhs_jac(v[V_Y], v[V_F], J);
+            if (!setup) return 1;
+        } else {
+            prob.rhs(v[V_Y], v[V_F]);
+            if (!setup) return 1;
+            prob.jac(v[V_Y], J);
+        }
+        return factor_from(J, gamma);
+    }
+    // M = I - gamma J, in-register LU with row partial pivoting (first index
+    // of largest magnitude).  Pivots are kept as an explicit permutation
+    // applied in solve().
+    int perm[N];
+    __device__ __forceinline__ int factor_from(const double (*J)[N], double gamma)
+    {
 #pragma unroll
         for (int i = 0; i < N; ++i)
 #pragma unroll

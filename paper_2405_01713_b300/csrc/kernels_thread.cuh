@@ -1,0 +1,122 @@
+// Device pieces shared by the translation units of the library: the cell
+// queue, the per-cell counters, the cooling-table staging and the
+// thread-per-cell kernel.  Both the context entry points (sunb_api.cu) and
+// the allocation-free one (sunb_noalloc.cu) launch this same kernel, so a
+// cell's arithmetic is identical through either.
+#pragma once
+#include <cstdint>
+
+#include "sunb_common.cuh"
+#include "bdf_control.cuh"
+#include "cell_thread.cuh"
+
+namespace sunb {
+
+// Cell indices handed out by a global counter (the device work queue):
+// a finished group or thread takes the next unstarted cell, so cells whose
+// step counts differ by orders of magnitude do not leave lanes idle.
+__device__ __forceinline__ long long grab_group(unsigned long long *q, int lane, unsigned mask, int L)
+{
+    unsigned long long v = 0;
+    if (lane == 0) v = atomicAdd(q, 1ull);
+    return (long long)__shfl_sync(mask, v, 0, L);
+}
+
+__device__ __forceinline__ long long grab_thread(unsigned long long *q)
+{
+    const unsigned m = __activemask();
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(m) - 1;
+    const int rank = __popc(m & ((1u << lane) - 1u));
+    unsigned long long base = 0;
+    if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(m));
+    base = __shfl_sync(m, base, leader);
+    return (long long)(base + rank);
+}
+
+__device__ __forceinline__ void write_stats(int32_t *stats, int32_t *status, long long cell,
+                                            const CellStats &s)
+{
+    int4 *p = reinterpret_cast<int4 *>(stats + 8 * cell);
+    p[0] = make_int4(s.nst, s.nfe, s.nje, s.nni);
+    p[1] = make_int4(s.ncf, s.nef, s.qlast, s.status);
+    if (status) status[cell] = s.status;
+}
+
+struct CoolArgs {
+    const double *knots;   // [3 * n + EXP_TABLE_SIZE]: lnT, lnLam, slope (n-1 used), exp table
+    int n;
+    double gamma_heat;
+};
+
+__device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned char *src, int bytes)
+{
+    const int4 *s = reinterpret_cast<const int4 *>(src);
+    int4 *d = reinterpret_cast<int4 *>(dst);
+    for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
+}
+
+__device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const CoolArgs &c)
+{
+    double *d = reinterpret_cast<double *>(dst);
+    for (int i = threadIdx.x; i < 3 * c.n + EXP_TABLE_SIZE; i += blockDim.x) d[i] = c.knots[i];
+    CoolingSmem t;
+    t.n = c.n;
+    t.gamma_heat = c.gamma_heat;
+    t.lnT = d;
+    t.lnLam = d + c.n;
+    t.slope = d + 2 * c.n;
+    t.exptab = d + 3 * c.n;
+    return t;
+}
+
+struct ThreadArgs {
+    long long n;
+    double *y;
+    const double *params;
+    int32_t *stats, *status;
+    unsigned long long *queue;
+    Controls ctl;
+    double atol[3];
+    CoolArgs cool;
+    int spread_lanes;   // > 0: one wave, lanes [0, spread_lanes) of every warp take a cell each
+};
+
+// Thread-per-cell kernel for Robertson and cosmology batches.  Large batches
+// take cells from the device queue; a batch that fits in one wave
+// (spread_lanes > 0) is spread over all SMs and warps instead, cell
+// b + grid (w + W l) for lane l < spread_lanes of warp w of CTA b, so that
+// few cells do not crowd a few SMs.
+template <class Prob>
+__global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
+{
+    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
+    CoolingSmem cool;
+    if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
+    __syncthreads();
+    ThreadCell<Prob> tc;
+    if constexpr (Prob::N == 1) tc.prob.tab = &cool;
+#pragma unroll
+    for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
+    bool taken = false;
+    run_cells(
+        tc, a.ctl, launched_warp_mask(),
+        [&]() -> long long {
+            if (a.spread_lanes > 0) {
+                const int l = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+                if (taken || l >= a.spread_lanes) return -1;
+                taken = true;
+                const long long cell = blockIdx.x + (long long)gridDim.x * (w + (long long)W * l);
+                return cell < a.n ? cell : -1;
+            }
+            const long long cell = grab_thread(a.queue);
+            return cell < a.n ? cell : -1;
+        },
+        [&](long long cell) {
+            tc.prob.load(a.params, cell);
+            tc.yg = a.y + cell * Prob::N;
+        },
+        [&](long long cell, const CellStats &st) { write_stats(a.stats, a.status, cell, st); });
+}
+
+}  // namespace sunb

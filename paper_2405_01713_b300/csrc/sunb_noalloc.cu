@@ -15,9 +15,7 @@
 #include <string>
 
 #include "sunb.h"
-#include "sunb_common.cuh"
-#include "bdf_control.cuh"
-#include "cell_thread.cuh"
+#include "kernels_thread.cuh"
 
 using namespace sunb;
 
@@ -58,49 +56,6 @@ int scratch_address(int device, void **out)
     }
     *out = g_scratch_addr[device];
     return SUNB_SUCCESS;
-}
-
-__device__ __forceinline__ long long noalloc_grab(unsigned long long *q)
-{
-    const unsigned m = __activemask();
-    const int lane = threadIdx.x & 31;
-    const int leader = __ffs(m) - 1;
-    const int rank = __popc(m & ((1u << lane) - 1u));
-    unsigned long long base = 0;
-    if (lane == leader) base = atomicAdd(q, (unsigned long long)__popc(m));
-    base = __shfl_sync(m, base, leader);
-    return (long long)(base + rank);
-}
-
-// The Robertson thread-per-cell integration with its scratch in the static
-// array: cells are taken from the queue counter at scratch[0], counters go
-// to scratch[256 + 32 c].
-__global__ void __launch_bounds__(256) robertson_noalloc_kernel(
-    const double *k, double *y, long long n, Controls ctl, double a0, double a1, double a2,
-    int32_t *status, unsigned char *scratch)
-{
-    unsigned long long *queue = reinterpret_cast<unsigned long long *>(scratch);
-    int32_t *stats = reinterpret_cast<int32_t *>(scratch + 256);
-    ThreadCell<RobertsonProblem> tc;
-    tc.atol[0] = a0;
-    tc.atol[1] = a1;
-    tc.atol[2] = a2;
-    run_cells(
-        tc, ctl, launched_warp_mask(),
-        [&]() -> long long {
-            const long long cell = noalloc_grab(queue);
-            return cell < n ? cell : -1;
-        },
-        [&](long long cell) {
-            tc.prob.load(k, cell);
-            tc.yg = y + 3 * cell;
-        },
-        [&](long long cell, const CellStats &s) {
-            int4 *p = reinterpret_cast<int4 *>(stats + 8 * cell);
-            p[0] = make_int4(s.nst, s.nfe, s.nje, s.nni);
-            p[1] = make_int4(s.ncf, s.nef, s.qlast, s.status);
-            if (status) status[cell] = s.status;
-        });
 }
 
 }  // namespace
@@ -145,13 +100,23 @@ extern "C" int sunb_integrate_robertson_noalloc(const double *dev_k, double *dev
     ctl.tout = tout;
     ctl.max_steps = max_steps > 0 ? max_steps : 100000;
     ctl.max_order = 5;
+    // the context path's thread-per-cell kernel, with the queue counter and
+    // the per-cell counters in the static scratch: the same cell arithmetic
+    ThreadArgs a{};
+    a.n = n_cells;
+    a.y = dev_y;
+    a.params = dev_k;
+    a.stats = reinterpret_cast<int32_t *>(static_cast<unsigned char *>(scratch) + 256);
+    a.status = dev_status;
+    a.queue = static_cast<unsigned long long *>(scratch);
+    a.ctl = ctl;
+    for (int i = 0; i < 3; ++i) a.atol[i] = host_atol[i];
+    a.spread_lanes = 0;
     int sms = 148;
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
     const long long want = (n_cells + 255) / 256;
     const int grid = (int)(want < 4LL * sms ? want : 4LL * sms);
-    robertson_noalloc_kernel<<<grid, 256, 0, s>>>(dev_k, dev_y, (long long)n_cells, ctl, host_atol[0],
-                                                  host_atol[1], host_atol[2], dev_status,
-                                                  static_cast<unsigned char *>(scratch));
+    thread_kernel<RobertsonProblem><<<grid, 256, 0, s>>>(a);
     e = cudaGetLastError();
     if (e != cudaSuccess) {
         sunb_internal_set_error(std::string("noalloc: launch: ") + cudaGetErrorString(e));
