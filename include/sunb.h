@@ -178,6 +178,14 @@ int sunb_lu_solve_batched_f32(int32_t n, int64_t batch, float *dev_A, int32_t *d
  * n < 0 or NULL arrays with n > 0 (message via sunb_last_error(NULL)). */
 int sunb_exp_check(const double *dev_x, double *dev_y, int64_t n, void *stream);
 
+/* The logarithm that the right-hand-side kernels use (table-driven after
+ * Tang 1990: 128 entries of 1/F and log F, F = 1 + j/128, degree-7
+ * polynomial for log1p on |r| < 1/128; the library log for zero, negative,
+ * subnormal, infinite and NaN x), applied to dev_x [n] into dev_y [n] on
+ * the given stream; returns after the result is written.  For checking its
+ * accuracy against log.  Errors as sunb_exp_check. */
+int sunb_log_check(const double *dev_x, double *dev_y, int64_t n, void *stream);
+
 /* Discrete adjoint (a differentiation extension of the path; the paper only
  * names the sensitivity-capable packages CVODES/IDAS, Sec. 2).  With
  * record_adjoint = cap > 0 at create, sunb_integrate records per cell and

@@ -80,6 +80,7 @@ SIGNATURES = {
     "sunb_lu_solve_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "sunb_lu_solve_batched_f32": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
     "sunb_exp_check": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
+    "sunb_log_check": (ctypes.c_int, [_vp, _vp, ctypes.c_int64, _vp]),
     "sunb_adjoint_replay": (ctypes.c_int, [_vp, _vp]),
     "sunb_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sunb_set_arrhenius": (ctypes.c_int, [_vp, _dp, _dp]),
@@ -300,6 +301,18 @@ def exp_check(x, stream=None):
     x = x.contiguous()
     y = torch.empty_like(x)
     _check(lib().sunb_exp_check(_ptr(x), _ptr(y), x.numel(), _stream_handle(stream)))
+    return y
+
+
+def log_check(x, stream=None):
+    """The logarithm of the right-hand-side kernels applied to a float64
+    CUDA tensor (a new tensor; for accuracy checks against log)."""
+    import torch
+    if not (x.is_cuda and x.dtype == torch.float64):
+        raise TypeError("x must be a float64 CUDA tensor")
+    x = x.contiguous()
+    y = torch.empty_like(x)
+    _check(lib().sunb_log_check(_ptr(x), _ptr(y), x.numel(), _stream_handle(stream)))
     return y
 
 

@@ -565,7 +565,7 @@ struct GroupCell {
         const double *y = V(sin);
         double *f = V(sout);
         const double T = y[K];
-        const double lnT = log(T), invT = rcp(T);
+        const double lnT = flog(T), invT = rcp(T);
         double s = 0.0;
         for (int k = g.lane; k < K; k += L) s += y[k] * tb.invW[k];
         s = g.sum(s);

@@ -59,7 +59,7 @@ struct CosmologyProblem {
     {
         const bool floor = e < 1.0;
         const double T = floor ? 1.0 : e;
-        const double lnT = log(T);
+        const double lnT = flog(T);
         const double *x = tab->lnT;
         const int n = tab->n;
         int lo;

@@ -503,6 +503,13 @@ __global__ void totals_kernel(const int32_t *stats, long long n, DevTotals *t)
 
 // ============================================================ host side
 
+// The right-hand sides' logarithm on a device array, for its accuracy test.
+__global__ void log_check_kernel(const double *x, double *y, long long n)
+{
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+        y[i] = flog(x[i]);
+}
+
 // The right-hand sides' exponential on a device array, for its accuracy test.
 __device__ double g_exp_tab[EXP_TABLE_SIZE];
 __global__ void exp_check_kernel(const double *x, double *y, long long n)
@@ -593,6 +600,21 @@ static int align16(int x) { return (x + 15) & ~15; }
 static void fill_exp_table(double *t)
 {
     for (int j = 0; j < EXP_TABLE_SIZE; ++j) t[j] = (double)exp2l((long double)j / (long double)EXP_TABLE_SIZE);
+}
+
+// 1/F, log F (hi, lo) for F = 1 + j/128 (the table of flog), into this
+// translation unit's g_log_tab on the current device.
+static int fill_log_table()
+{
+    double t[3 * LOG_TABLE_SIZE];
+    for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
+        const long double F = 1.0L + (long double)j / (long double)LOG_TABLE_SIZE;
+        const long double lf = logl(F);
+        t[j] = (double)(1.0L / F);
+        t[LOG_TABLE_SIZE + j] = (double)lf;
+        t[2 * LOG_TABLE_SIZE + j] = (double)(lf - (long double)t[LOG_TABLE_SIZE + j]);
+    }
+    return cudaMemcpyToSymbol(g_log_tab, t, sizeof(t)) == cudaSuccess ? SUNB_SUCCESS : SUNB_CUDA_ERROR;
 }
 
 static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
@@ -1112,6 +1134,7 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
     if (lpc != 0 && lpc != 8 && lpc != 16 && lpc != 32) { fail(ctx, SUNB_ILL_INPUT, "lanes_per_cell must be 0, 8, 16 or 32"); return bail(SUNB_ILL_INPUT); }
     int rc;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "no CUDA device"); return bail(SUNB_CUDA_ERROR); }
+    if (fill_log_table() != SUNB_SUCCESS) { fail(ctx, SUNB_CUDA_ERROR, "log table copy failed"); return bail(SUNB_CUDA_ERROR); }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
 
     if (ctx->kind == SUNB_ROBERTSON) ctx->N = 3;
@@ -1387,6 +1410,27 @@ int sunb_exp_check(const double *dev_x, double *dev_y, int64_t n, void *stream)
     // the host table must outlive the asynchronous copy
     if (cudaStreamSynchronize(st) != cudaSuccess) {
         g_create_error = "exp_check: kernel failed";
+        return SUNB_CUDA_ERROR;
+    }
+    return SUNB_SUCCESS;
+}
+
+int sunb_log_check(const double *dev_x, double *dev_y, int64_t n, void *stream)
+{
+    if (n < 0 || (n > 0 && (!dev_x || !dev_y))) {
+        g_create_error = "log_check: need n >= 0 and device arrays";
+        return SUNB_ILL_INPUT;
+    }
+    if (n == 0) return SUNB_SUCCESS;
+    if (fill_log_table() != SUNB_SUCCESS) {
+        g_create_error = "log_check: table copy failed";
+        return SUNB_CUDA_ERROR;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    const int grid = (int)std::min<long long>((n + 255) / 256, 148 * 8);
+    log_check_kernel<<<grid, 256, 0, st>>>(dev_x, dev_y, (long long)n);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess) {
+        g_create_error = "log_check: kernel failed";
         return SUNB_CUDA_ERROR;
     }
     return SUNB_SUCCESS;

@@ -11,6 +11,44 @@
 
 namespace sunb {
 
+// ---------------- logarithm used by the right-hand sides ----------------
+// log(x) by table-driven reduction (P. T. P. Tang, "Table-driven
+// implementation of the logarithm function in IEEE floating-point
+// arithmetic", ACM TOMS 16(4), 1990), with 128 table entries:
+//   x = 2^m (F + f),  F = 1 + j/128 (the leading 7 mantissa bits),
+//   0 <= f < 1/128,  log x = m ln2 + log F + log1p(f/F),
+// f exact (Sterbenz), f/F = f * (1/F) from the table, log1p(r) by its
+// degree-7 Taylor polynomial (|r| < 1/128: truncation below 2e-18).  ln2 is
+// split as LN2_HI (42 significant bits, so m LN2_HI is exact) + LN2_LO, and
+// log F as hi + lo in the table.  g_log_tab[j] = 1/F, [128 + j] = log F
+// (hi), [256 + j] = log F (lo), filled by the host (fill_log_table) in every
+// translation unit that evaluates it.  Zero, negative, subnormal, infinite
+// and NaN x go to the library log.  Error: within 2 ulp of log x, and
+// within 4e-16 absolute where log x is small and m != 0 (x just below 1).
+constexpr int LOG_TABLE_SIZE = 128;   // the shift below (>> 13, & 127) assumes 128
+static __device__ double g_log_tab[3 * LOG_TABLE_SIZE];
+
+__device__ __forceinline__ double flog(double x)
+{
+    const int hi = __double2hiint(x);
+    if (hi < 0x00100000 || hi >= 0x7ff00000) return log(x);  // not a positive normal number
+    const int m = (hi >> 20) - 1023;
+    const int j = (hi >> 13) & (LOG_TABLE_SIZE - 1);
+    const double xm = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));   // [1, 2)
+    const double F = __hiloint2double(0x3ff00000 | (j << 13), 0);                            // 1 + j/128
+    const double r = (xm - F) * __ldg(g_log_tab + j);
+    double q = fma(r, 1.0 / 7.0, -1.0 / 6.0);
+    q = fma(r, q, 1.0 / 5.0);
+    q = fma(r, q, -0.25);
+    q = fma(r, q, 1.0 / 3.0);
+    q = fma(r, q, -0.5);
+    const double s = (r * r) * q;                                // log1p(r) - r
+    const double md = (double)m;
+    const double h = fma(md, 0x1.62e42fefa3800p-1, __ldg(g_log_tab + LOG_TABLE_SIZE + j));
+    const double l = fma(md, 0x1.ef35793c76730p-45, __ldg(g_log_tab + 2 * LOG_TABLE_SIZE + j));
+    return h + (r + (s + l));
+}
+
 // ---------------- exponential used by the right-hand sides ----------------
 // exp(x) by table-driven range reduction (P. T. P. Tang, "Table-driven
 // implementation of the exponential function in IEEE floating-point

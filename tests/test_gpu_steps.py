@@ -181,3 +181,33 @@ def test_rhs_exponential_within_two_ulp_of_exp():
     assert torch.equal(y[~inside], ref[~inside])
     nan = m.exp_check(torch.tensor([float("nan")], dtype=torch.float64, device="cuda"))
     assert torch.isnan(nan).all()
+
+
+def test_rhs_logarithm_against_log():
+    """The table-driven logarithm of the right-hand sides against the
+    library log: within 2 ulp of log x, or 4e-16 absolute where log x is
+    small (x just below 1); the library's result outside positive normal
+    numbers; exact at 1 and at powers of two times table nodes."""
+    need_gpu()
+    m = sb()
+    g = torch.Generator(device="cpu").manual_seed(6)
+    parts = [
+        torch.exp((torch.rand(2_000_000, generator=g, dtype=torch.float64) * 2 - 1) * 700),
+        1.0 + (torch.rand(200_000, generator=g, dtype=torch.float64) * 2 - 1) * 0.07,
+        torch.rand(200_000, generator=g, dtype=torch.float64) * 1e4,
+        (1.0 + torch.arange(128, dtype=torch.float64) / 128) * 2.0 ** 10,
+        torch.tensor([1.0, 2.0, 0.5, 1e-300, 1e300, 2.2250738585072014e-308, 1.7e308,
+                      5e-324, 0.0, -0.0, -1.0, float("inf")], dtype=torch.float64),
+    ]
+    x = torch.cat(parts).cuda()
+    y = m.log_check(x)
+    ref = torch.log(x)
+    assert torch.all(y[x == 1.0] == 0.0)
+    normal = (x >= 2.2250738585072014e-308) & torch.isfinite(x)
+    ulp = (torch.nextafter(ref.abs(), torch.full_like(ref, float("inf"))) - ref.abs())[normal]
+    err = (y - ref)[normal].abs()
+    assert torch.all(err <= torch.maximum(2.0 * ulp, torch.full_like(ulp, 4e-16))), \
+        float((err / ulp).max())
+    assert torch.equal(y[~normal & ~torch.isnan(ref)], ref[~normal & ~torch.isnan(ref)])
+    nan = m.log_check(torch.tensor([float("nan"), -2.0], dtype=torch.float64, device="cuda"))
+    assert torch.isnan(nan).all()
