@@ -74,7 +74,7 @@ __device__ __forceinline__ double eta_from(double d2, int p, double bias)
 {
     const double inv_p1[7] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0};
     // (bias * sqrt(d2))^(1/(p+1)) = exp(0.5 * log(bias^2 d2) / (p+1))
-    double r = exp(0.5 * log(bias * bias * d2) * inv_p1[p]);
+    double r = fexp(0.5 * flog(bias * bias * d2) * inv_p1[p], g_exp_tab);
     return rcp(r + 1e-6);
 }
 

@@ -511,7 +511,6 @@ __global__ void log_check_kernel(const double *x, double *y, long long n)
 }
 
 // The right-hand sides' exponential on a device array, for its accuracy test.
-__device__ double g_exp_tab[EXP_TABLE_SIZE];
 __global__ void exp_check_kernel(const double *x, double *y, long long n)
 {
     for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
@@ -595,27 +594,6 @@ static int fail(sunb_ctx *ctx, int code, const std::string &msg)
     } while (0)
 
 static int align16(int x) { return (x + 15) & ~15; }
-
-// 2^(j/64), j < EXP_TABLE_SIZE, rounded to double (the table of fexp).
-static void fill_exp_table(double *t)
-{
-    for (int j = 0; j < EXP_TABLE_SIZE; ++j) t[j] = (double)exp2l((long double)j / (long double)EXP_TABLE_SIZE);
-}
-
-// 1/F, log F (hi, lo) for F = 1 + j/128 (the table of flog), into this
-// translation unit's g_log_tab on the current device.
-static int fill_log_table()
-{
-    double t[3 * LOG_TABLE_SIZE];
-    for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
-        const long double F = 1.0L + (long double)j / (long double)LOG_TABLE_SIZE;
-        const long double lf = logl(F);
-        t[j] = (double)(1.0L / F);
-        t[LOG_TABLE_SIZE + j] = (double)lf;
-        t[2 * LOG_TABLE_SIZE + j] = (double)(lf - (long double)t[LOG_TABLE_SIZE + j]);
-    }
-    return cudaMemcpyToSymbol(g_log_tab, t, sizeof(t)) == cudaSuccess ? SUNB_SUCCESS : SUNB_CUDA_ERROR;
-}
 
 static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
 {
@@ -704,7 +682,7 @@ static int build_mech_blob(sunb_ctx *ctx, const sunb_mechanism *m)
     }
     I(o.inc_ptr)[K] = e;
     std::memcpy(blob.data() + o.ridx, ridx.data(), 4 * 2 * M);
-    fill_exp_table(D(o.exptab));
+    exp_table_values(D(o.exptab));
     ctx->off = o;
     ctx->blob.swap(blob);
     return SUNB_SUCCESS;
@@ -1134,7 +1112,7 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
     if (lpc != 0 && lpc != 8 && lpc != 16 && lpc != 32) { fail(ctx, SUNB_ILL_INPUT, "lanes_per_cell must be 0, 8, 16 or 32"); return bail(SUNB_ILL_INPUT); }
     int rc;
     if (cudaGetDevice(&ctx->device) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "no CUDA device"); return bail(SUNB_CUDA_ERROR); }
-    if (fill_log_table() != SUNB_SUCCESS) { fail(ctx, SUNB_CUDA_ERROR, "log table copy failed"); return bail(SUNB_CUDA_ERROR); }
+    if (fill_math_tables() != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "math table copy failed"); return bail(SUNB_CUDA_ERROR); }
     cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, ctx->device);
 
     if (ctx->kind == SUNB_ROBERTSON) ctx->N = 3;
@@ -1151,7 +1129,7 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
             return bail(SUNB_ILL_INPUT);
         }
         std::vector<double> k(3 * t->n_knots + EXP_TABLE_SIZE, 0.0);
-        fill_exp_table(k.data() + 3 * t->n_knots);
+        exp_table_values(k.data() + 3 * t->n_knots);
         for (int i = 0; i < t->n_knots; ++i) {
             k[i] = t->lnT[i];
             k[t->n_knots + i] = t->lnLam[i];
@@ -1394,13 +1372,11 @@ int sunb_exp_check(const double *dev_x, double *dev_y, int64_t n, void *stream)
         return SUNB_ILL_INPUT;
     }
     if (n == 0) return SUNB_SUCCESS;
-    double tab[EXP_TABLE_SIZE];
-    fill_exp_table(tab);
-    cudaStream_t st = (cudaStream_t)stream;
-    if (cudaMemcpyToSymbolAsync(g_exp_tab, tab, sizeof(tab), 0, cudaMemcpyHostToDevice, st) != cudaSuccess) {
+    if (fill_math_tables() != cudaSuccess) {
         g_create_error = "exp_check: table copy failed";
         return SUNB_CUDA_ERROR;
     }
+    cudaStream_t st = (cudaStream_t)stream;
     const int grid = (int)std::min<long long>((n + 255) / 256, 148 * 8);
     exp_check_kernel<<<grid, 256, 0, st>>>(dev_x, dev_y, (long long)n);
     if (cudaGetLastError() != cudaSuccess) {
@@ -1422,7 +1398,7 @@ int sunb_log_check(const double *dev_x, double *dev_y, int64_t n, void *stream)
         return SUNB_ILL_INPUT;
     }
     if (n == 0) return SUNB_SUCCESS;
-    if (fill_log_table() != SUNB_SUCCESS) {
+    if (fill_math_tables() != cudaSuccess) {
         g_create_error = "log_check: table copy failed";
         return SUNB_CUDA_ERROR;
     }

@@ -6,6 +6,7 @@
 // stopped by Eq. stop_newton (c_eps = 0.1, c_r = 0.3) on I - gamma J with a
 // dense Jacobian and a pivoted LU (Table 1 approach 2A; Sec. 4.1.4, 4.1.6).
 #pragma once
+#include <cmath>
 #include <cstdint>
 #include <cuda_runtime.h>
 
@@ -21,8 +22,8 @@ namespace sunb {
 // degree-7 Taylor polynomial (|r| < 1/128: truncation below 2e-18).  ln2 is
 // split as LN2_HI (42 significant bits, so m LN2_HI is exact) + LN2_LO, and
 // log F as hi + lo in the table.  g_log_tab[j] = 1/F, [128 + j] = log F
-// (hi), [256 + j] = log F (lo), filled by the host (fill_log_table) in every
-// translation unit that evaluates it.  Zero, negative, subnormal, infinite
+// (hi), [256 + j] = log F (lo), filled by the host (fill_math_tables) in
+// every translation unit that evaluates it.  Zero, negative, subnormal, infinite
 // and NaN x go to the library log.  Error: within 2 ulp of log x, and
 // within 4e-16 absolute where log x is small and m != 0 (x just below 1).
 constexpr int LOG_TABLE_SIZE = 128;   // the shift below (>> 13, & 127) assumes 128
@@ -59,10 +60,12 @@ __device__ __forceinline__ double flog(double x)
 // relative).  ln2/64 is split as C1 + C2 with C1 of 32 significant bits, so
 // that n C1 is exact; n is the nearest integer to 64 x/ln2, read from the
 // low word of x 64/ln2 + 1.5*2^52.  tab[j] = 2^(j/64) rounded to double
-// (EXP_TABLE_SIZE entries, filled by the host).  For |x| >= 704, where
+// (EXP_TABLE_SIZE entries: a shared-memory copy in the kernels, or
+// g_exp_tab, filled by fill_math_tables).  For |x| >= 704, where
 // 2^m would leave the normal range, and for NaN the library exp is used.
 // Accuracy: within 2 ulp of exp (checked against it by the GPU tests).
 constexpr int EXP_TABLE_SIZE = 64;   // the shifts below (>> 6, & 63) assume 64
+static __device__ double g_exp_tab[EXP_TABLE_SIZE];
 __device__ __forceinline__ double fexp(double x, const double *__restrict__ tab)
 {
     if (!(fabs(x) < 704.0)) return exp(x);
@@ -137,5 +140,32 @@ enum Vec : int {
 };
 
 __device__ __forceinline__ double rcp(double x) { return __drcp_rn(x); }
+
+// ---------------- host side of the math tables ----------------
+// 2^(j/64) rounded to double: the table of fexp.
+static inline void exp_table_values(double *t)
+{
+    for (int j = 0; j < EXP_TABLE_SIZE; ++j) t[j] = (double)exp2l((long double)j / (long double)EXP_TABLE_SIZE);
+}
+
+// This translation unit's g_exp_tab and g_log_tab on the current device
+// (1/F and log F in two parts for F = 1 + j/128).  Returns cudaSuccess or
+// the copy's error.
+static inline cudaError_t fill_math_tables()
+{
+    double e[EXP_TABLE_SIZE];
+    exp_table_values(e);
+    double t[3 * LOG_TABLE_SIZE];
+    for (int j = 0; j < LOG_TABLE_SIZE; ++j) {
+        const long double F = 1.0L + (long double)j / (long double)LOG_TABLE_SIZE;
+        const long double lf = logl(F);
+        t[j] = (double)(1.0L / F);
+        t[LOG_TABLE_SIZE + j] = (double)lf;
+        t[2 * LOG_TABLE_SIZE + j] = (double)(lf - (long double)t[LOG_TABLE_SIZE + j]);
+    }
+    const cudaError_t a = cudaMemcpyToSymbol(g_exp_tab, e, sizeof(e));
+    const cudaError_t b = cudaMemcpyToSymbol(g_log_tab, t, sizeof(t));
+    return a != cudaSuccess ? a : b;
+}
 
 }  // namespace sunb

@@ -52,6 +52,12 @@ int scratch_address(int device, void **out)
                                     cudaGetErrorString(e));
             return SUNB_CUDA_ERROR;
         }
+        // the step-size choice evaluates this unit's exp and log tables
+        const cudaError_t t = fill_math_tables();
+        if (t != cudaSuccess) {
+            sunb_internal_set_error(std::string("noalloc: math table copy failed: ") + cudaGetErrorString(t));
+            return SUNB_CUDA_ERROR;
+        }
         g_scratch_addr[device] = p;
     }
     *out = g_scratch_addr[device];
