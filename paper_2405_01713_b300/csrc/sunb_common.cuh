@@ -26,13 +26,18 @@ namespace sunb {
 // every translation unit that evaluates it.  Zero, negative, subnormal, infinite
 // and NaN x go to the library log.  Error: within 2 ulp of log x, and
 // within 4e-16 absolute where log x is small and m != 0 (x just below 1).
+// The library functions for the arguments the table methods leave out: out
+// of line, so that their code is not repeated at every call site.
+__device__ __noinline__ double log_outside(double x) { return log(x); }
+__device__ __noinline__ double exp_outside(double x) { return exp(x); }
+
 constexpr int LOG_TABLE_SIZE = 128;   // the shift below (>> 13, & 127) assumes 128
 static __device__ double g_log_tab[3 * LOG_TABLE_SIZE];
 
 __device__ __forceinline__ double flog(double x)
 {
     const int hi = __double2hiint(x);
-    if (hi < 0x00100000 || hi >= 0x7ff00000) return log(x);  // not a positive normal number
+    if (hi < 0x00100000 || hi >= 0x7ff00000) return log_outside(x);   // not a positive normal number
     const int m = (hi >> 20) - 1023;
     const int j = (hi >> 13) & (LOG_TABLE_SIZE - 1);
     const double xm = __hiloint2double((hi & 0x000fffff) | 0x3ff00000, __double2loint(x));   // [1, 2)
@@ -68,7 +73,7 @@ constexpr int EXP_TABLE_SIZE = 64;   // the shifts below (>> 6, & 63) assume 64
 static __device__ double g_exp_tab[EXP_TABLE_SIZE];
 __device__ __forceinline__ double fexp(double x, const double *__restrict__ tab)
 {
-    if (!(fabs(x) < 704.0)) return exp(x);
+    if (!(fabs(x) < 704.0)) return exp_outside(x);
     const double shift = 6755399441055744.0;                 // 1.5 * 2^52
     const double t = fma(x, 0x1.71547652b82fep+6, shift);    // 64 / ln 2
     const int n = __double2loint(t);
