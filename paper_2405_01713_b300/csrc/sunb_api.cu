@@ -245,7 +245,8 @@ __global__ void __launch_bounds__(128) lu_batched_kernel(int n, long long batch,
 // Discrete adjoint of the recorded forward map (a lane group per cell, FP64).
 // Replay: recompute the step history from the tape header (y0, h0) with each
 // corrector solved to rounding level (Newton with the analytic Jacobian at
-// the recorded state), overwriting the tape's states with these exact ones.
+// the recorded state, the matrix in FP32 and the residual in FP64),
+// overwriting the tape's states with these exact ones.
 // Reverse: lam (the adjoint of the Nordsieck array) is carried back through
 // each step's update, corrector (mu = (I - gamma J(y_n))^{-T} lam_Delta),
 // prediction and column map, accumulating gamma (df/dtheta)^T mu for
@@ -281,8 +282,8 @@ __device__ void adj_theta(GroupCell<L, double> &c, const double *mu, double scal
     c.g.sync();
 }
 
-template <int L>
-__device__ void adj_bind(GroupCell<L, double> &c, unsigned char *smem, const MechArgs &m, int gid)
+template <int L, typename MT>
+__device__ void adj_bind(GroupCell<L, MT> &c, unsigned char *smem, const MechArgs &m, int gid)
 {
     c.g.lane = threadIdx.x % L;
     c.g.mask = group_mask<L>();
@@ -293,14 +294,14 @@ __device__ void adj_bind(GroupCell<L, double> &c, unsigned char *smem, const Mec
     c.tape = nullptr;
 }
 
-template <int L>
+template <int L, typename MT>
 __global__ void __launch_bounds__(256) adjoint_replay_kernel(const AdjArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
     stage_bytes(smem, a.m.tab, a.m.off.bytes);
     __syncthreads();
-    GroupCell<L, double> c;
-    adj_bind<L>(c, smem, a.m, threadIdx.x / L);
+    GroupCell<L, MT> c;
+    adj_bind<L, MT>(c, smem, a.m, threadIdx.x / L);
     const int N = c.N, H = tape_header(N), R = tape_record(N);
     for (;;) {
         const long long cell = grab_group(a.m.queue, c.g.lane, c.g.mask, L);
@@ -382,7 +383,7 @@ __global__ void __launch_bounds__(256) adjoint_reverse_kernel(const AdjArgs a)
     stage_bytes(smem, a.m.tab, a.m.off.bytes);
     __syncthreads();
     GroupCell<L, double> c;
-    adj_bind<L>(c, smem, a.m, threadIdx.x / L);
+    adj_bind<L, double>(c, smem, a.m, threadIdx.x / L);
     const int N = c.N, M = c.M, H = tape_header(N), R = tape_record(N);
     for (;;) {
         const long long cell = grab_group(a.m.queue, c.g.lane, c.g.mask, L);
@@ -962,7 +963,7 @@ static int eval_config(sunb_ctx *ctx, MechArgs &a, int &bytes)
 template <int L>
 static void *adj_kernel(int mode)
 {
-    return mode == 0 ? (void *)adjoint_replay_kernel<L> : (void *)adjoint_reverse_kernel<L>;
+    return mode == 0 ? (void *)adjoint_replay_kernel<L, float> : (void *)adjoint_reverse_kernel<L>;
 }
 
 // Adjoint kernels: 16 lanes per cell (on B300 the replay and reverse sweep
@@ -974,7 +975,10 @@ static int adj_launch(sunb_ctx *ctx, int mode, const double *dLdy, double *yrep)
     constexpr int L = 16;
     AdjArgs a{};
     a.m = mech_args(ctx, nullptr, 0.0, 0.0, nullptr);
-    a.m.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, 8);
+    // the replay's Newton matrix only steers an iteration whose residual is
+    // formed in FP64, so it converges to the same FP64 corrector in FP32; the
+    // reverse sweep's transposed solve defines the gradient: FP64
+    a.m.lay = make_layout(ctx->off.N, ctx->off.K, ctx->off.M, mode == 0 ? 4 : 8);
     a.dLdy = dLdy;
     a.yrep = yrep;
     a.gcells = ctx->d_gcells;

@@ -28,8 +28,8 @@ namespace sunb {
 // within 4e-16 absolute where log x is small and m != 0 (x just below 1).
 // The library functions for the arguments the table methods leave out: out
 // of line, so that their code is not repeated at every call site.
-__device__ __noinline__ double log_outside(double x) { return log(x); }
-__device__ __noinline__ double exp_outside(double x) { return exp(x); }
+static __device__ __noinline__ double log_outside(double x) { return log(x); }
+static __device__ __noinline__ double exp_outside(double x) { return exp(x); }
 
 constexpr int LOG_TABLE_SIZE = 128;   // the shift below (>> 13, & 127) assumes 128
 static __device__ double g_log_tab[3 * LOG_TABLE_SIZE];
