@@ -64,8 +64,8 @@ def jac_extra_flops(mech):
 # cells (traffic is per cell: y in and out, parameters, counters):
 #   ncu --set full --clock-control none -k regex:mech_kernel -c 1 python bench.py
 #       --workload mech22 --cells 7168 --lanes 8 --steps 1 --warmup 1 --no-plain --no-cpu --no-e2e
-# -> 1.70 MB + 2.21 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md).
-TRAFFIC_BYTES_PER_CELL = {"mech22": 545.0}
+# -> 1.716 MB + 1.627 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md).
+TRAFFIC_BYTES_PER_CELL = {"mech22": 466.4}
 
 
 def work_model(kind, mech, tot):
