@@ -163,8 +163,18 @@ struct CellRun {
         phase = PH_DONE;
     }
 
-    // first steps of a cell: load, f(t0, y0), weights, starting step size
-    __device__ void begin(C &c, const Controls &ctl)
+    // first steps of a cell: load, f(t0, y0), weights, starting step size.
+    // Backends that ask for it (C::kOutlineRare) run this and the failure
+    // paths out of line, so that the kernel's hot loop carries less code
+    // (instruction fetch is one of the lane-group kernel's leading stalls);
+    // for thread-per-cell cells they are too frequent to pay a call.
+    __device__ __forceinline__ void begin(C &c, const Controls &ctl)
+    {
+        if constexpr (C::kOutlineRare) begin_outlined(c, ctl);
+        else begin_body(c, ctl);
+    }
+    __device__ __noinline__ void begin_outlined(C &c, const Controls &ctl) { begin_body(c, ctl); }
+    __device__ __forceinline__ void begin_body(C &c, const Controls &ctl)
     {
         const double t0 = ctl.t0;
         tout = ctl.tout;
@@ -175,7 +185,7 @@ struct CellRun {
         q = 1;
         c.load_y(V_Z0);
         if (!(tout > t0)) { finish(c); return; }
-        c.rhs(V_Z0, V_F);
+        c.rhs_start(V_Z0, V_F);
         s.nfe++;
         if (!c.all_finite(V_F) || !c.all_finite(V_Z0)) {
             s.status = ST_NONFINITE;
@@ -190,7 +200,7 @@ struct CellRun {
             double h0 = (d0 < 1e-10 || d1 < 1e-10) ? 1e-6 * span : 0.01 * sqrt(d0 * rcp(d1));
             if (h0 > span) h0 = span;
             c.axpby(V_Y, 1.0, V_Z0, h0, V_F);
-            c.rhs(V_Y, V_DEL);
+            c.rhs_start(V_Y, V_DEL);
             s.nfe++;
             const double rh0 = rcp(h0);
             const double d2 = c.wrms2_lin(rh0, V_DEL, -rh0, V_F);
@@ -317,18 +327,37 @@ struct CellRun {
             return;
         }
         if (!conv) {                  // Newton failure
-            c.unpredict(q);
-            s.ncf++; ncf++;
-            if (ncf >= MXNCF) { s.status = ST_CONV_FAILURE; finish(c); return; }
-            h *= ETA_CF;
-            c.rescale(q, ETA_CF);
-            force_setup = 1; etamax = 1.0; last = 0; nsame = 0;
-            if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
-            phase = PH_ATTEMPT;
+            if constexpr (C::kOutlineRare) fail_newton_outlined(c);
+            else fail_newton(c);
             return;
         }
         dsm2 = (Cq * Cq) * c.wrms2(V_ACOR);
         if (dsm2 >= 1.0) {            // error-test failure (accept iff ||LTE|| < 1)
+            if constexpr (C::kOutlineRare) fail_error_outlined(c);
+            else fail_error(c);
+            return;
+        }
+        accept_step(c);
+    }
+
+    // the rarer outcomes of an attempt (out of line for C::kOutlineRare)
+    __device__ __noinline__ void fail_newton_outlined(C &c) { fail_newton(c); }
+    __device__ __noinline__ void fail_error_outlined(C &c) { fail_error(c); }
+    __device__ __forceinline__ void fail_newton(C &c)
+    {
+        c.unpredict(q);
+        s.ncf++; ncf++;
+        if (ncf >= MXNCF) { s.status = ST_CONV_FAILURE; finish(c); return; }
+        h *= ETA_CF;
+        c.rescale(q, ETA_CF);
+        force_setup = 1; etamax = 1.0; last = 0; nsame = 0;
+        if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
+        phase = PH_ATTEMPT;
+    }
+
+    __device__ __forceinline__ void fail_error(C &c)
+    {
+        {
             c.unpredict(q);
             s.nef++; nef++;
             if (nef >= MXNEF) { s.status = ST_ERR_FAILURE; finish(c); return; }
@@ -379,10 +408,11 @@ struct CellRun {
             etamax = 1.0; last = 0; nsame = 0;
             if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
             phase = PH_ATTEMPT;
-            return;
         }
+    }
 
-        // ---- accepted step ----
+    __device__ __forceinline__ void accept_step(C &c)
+    {
         s.nst++;
         t = last ? tout : t + h;
         c.correct(q, l);

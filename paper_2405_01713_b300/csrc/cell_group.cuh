@@ -234,6 +234,8 @@ struct GroupCell {
     // iteration takes it in the next superstep, at the same f call site as
     // the first iterations of the other groups of its warp
     static constexpr bool kNewtonLoop = false;
+    // the starting step and the failure paths out of line (see CellRun)
+    static constexpr bool kOutlineRare = true;
     Grp<L> g;
     MechTab tb;
     int N, K, M, NP;
@@ -325,9 +327,18 @@ struct GroupCell {
         for (int i = g.lane; i < 36; i += L) Pm[i] = (i % 7 == 0) ? 1.0 : 0.0;
         g.sync();
     }
-    __device__ void rec_init(double h0)
+    // recording only with a tape; the recording code out of line
+    __device__ __forceinline__ void rec_init(double h0)
     {
-        if (!tape) return;
+        if (tape) rec_init_body(h0);
+    }
+    __device__ __forceinline__ void rec_accept(int q, int qo, const double *l, double inv_xi, double gamma,
+                                               double il1)
+    {
+        if (tape) rec_accept_body(q, qo, l, inv_xi, gamma, il1);
+    }
+    __device__ __noinline__ void rec_init_body(double h0)
+    {
         const double *z0 = V(V_Z0);
         for (int i = g.lane; i < N; i += L) tape[8 + i] = z0[i];
         if (g.lane == 0) { tape[0] = 0.0; tape[1] = h0; tape[2] = 0.0; }
@@ -336,9 +347,9 @@ struct GroupCell {
     }
     // one accepted step: y_n (= z0 after the correction), the map, the
     // update vector (with the terms of an order increase), gamma, 1/l_1
-    __device__ void rec_accept(int q, int qo, const double *l, double inv_xi, double gamma, double il1)
+    __device__ __noinline__ void rec_accept_body(int q, int qo, const double *l, double inv_xi, double gamma,
+                                                 double il1)
     {
-        if (!tape) return;
         if (rec_count >= tape_cap) {
             if (g.lane == 0) tape[2] = 1.0;
             return;
@@ -738,6 +749,9 @@ struct GroupCell {
     }
 
     __device__ __forceinline__ void rhs(int a, int b) { eval(a, b, 0.0, false); }
+    // the starting step's f evaluations (once per cell): out of line, so
+    // that the kernel's hot loop does not carry two more copies of eval
+    __device__ __noinline__ void rhs_start(int a, int b) { eval(a, b, 0.0, false); }
     __device__ __forceinline__ int rhs_setup(int a, int b, double gamma)
     {
         eval(a, b, gamma, true);

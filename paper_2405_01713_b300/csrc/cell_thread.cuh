@@ -103,6 +103,7 @@ struct ThreadCell {
     // all Newton iterations of an attempt in one superstep: the control
     // logic (cheap f, costly control) then stays aligned across the warp
     static constexpr bool kNewtonLoop = true;
+    static constexpr bool kOutlineRare = false;
     Prob prob;
     double v[NVEC][N];
     double M[N][N];
@@ -123,6 +124,7 @@ struct ThreadCell {
         for (int i = 0; i < N; ++i) yg[i] = v[s][i];
     }
     __device__ __forceinline__ void rhs(int a, int b) { prob.rhs(v[a], v[b]); }
+    __device__ __forceinline__ void rhs_start(int a, int b) { prob.rhs(v[a], v[b]); }
     __device__ __forceinline__ bool all_finite(int a) const
     {
         bool ok = true;
