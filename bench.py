@@ -64,8 +64,10 @@ def jac_extra_flops(mech):
 # cells (traffic is per cell: y in and out, parameters, counters):
 #   ncu --set full --clock-control none -k regex:mech_kernel -c 1 python bench.py
 #       --workload mech22 --cells 7168 --lanes 8 --steps 1 --warmup 1 --no-plain --no-cpu --no-e2e
-# -> 1.716 MB + 1.627 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md).
-TRAFFIC_BYTES_PER_CELL = {"mech22": 466.4}
+# -> 1.660 MB + 31.598 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md):
+# y, parameters and counters (~400 B) plus the write-back of the out-of-line
+# calls' stack frames.
+TRAFFIC_BYTES_PER_CELL = {"mech22": 4639.7}
 
 
 def work_model(kind, mech, tot):

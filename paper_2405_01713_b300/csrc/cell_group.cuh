@@ -752,11 +752,6 @@ struct GroupCell {
     // the starting step's f evaluations (once per cell): out of line, so
     // that the kernel's hot loop does not carry two more copies of eval
     __device__ __noinline__ void rhs_start(int a, int b) { eval(a, b, 0.0, false); }
-    __device__ __forceinline__ int rhs_setup(int a, int b, double gamma)
-    {
-        eval(a, b, gamma, true);
-        return factor();
-    }
     // The f evaluation of a Newton iteration, f(y) into V_F; with setup also
     // the Newton matrix at y, factored (0: singular).  One call site for
     // both, so groups of a warp that set up and groups that do not share
