@@ -257,8 +257,10 @@ int sunb_destroy(sunb_ctx *ctx);
  *    until the process exits; it limits n_cells to 65536 (larger batches
  *    return SUNB_ILL_INPUT before anything is enqueued).
  *  - The first call on a device looks up that array's device address (with
- *    the device current) and caches it; make that first call before any
- *    stream capture.  The counter is cleared on every call.
+ *    the device current) and caches it, and copies the step-size choice's
+ *    exp and log tables (3.6 KB of constants, into static device arrays)
+ *    with a synchronous copy; make that first call before any stream
+ *    capture.  The counter is cleared on every call.
  *  - All calls share the array: calls whose work overlaps on the GPU (on
  *    different streams, or from several host threads) race; serialise them.
  *  - Asynchronous on stream; returns launch errors only; errors are
