@@ -93,6 +93,7 @@ def lib():
         L.orc_adjoint_sqerr.argtypes = [PP, ctypes.c_long, _dp, _dp, ctypes.c_double, ctypes.c_double,
                                         ctypes.POINTER(Options), ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.orc_adjoint_sqerr.restype = ctypes.c_int
+        L.orc_typical_atol.argtypes = [_dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, _dp]
         _lib = L
     return _lib
 
@@ -172,6 +173,18 @@ def jac(pb, y, cell=0, mode=0, w=None):
     J = np.empty((pb.n, pb.n))
     lib().orc_jac(pb.ref, cell, _d(y), _d(f), _d(w), mode, _d(J))
     return J
+
+
+def typical_atol(y, eta=1e-10):
+    """Typical-value absolute tolerances of a batch y [C, n] (Sec. 4.1.3,
+    Eq. eta): eta * (min + max)/2 per component, 1 * eta where that is not
+    a positive finite number."""
+    y = _f64(y)
+    if y.ndim == 1:
+        y = y.reshape(-1, 1)
+    out = np.empty(y.shape[1])
+    lib().orc_typical_atol(_d(y), y.shape[0], y.shape[1], float(eta), _d(out))
+    return out
 
 
 def lu_factor(A):

@@ -176,6 +176,30 @@ static void bdf_xi(int m, double h, const double *hist, double *xi)
 }
 
 /* l[0..q]: coefficients of Lambda(x) = prod_{i=1..q} (1 + x/xi_i). */
+/* Typical-value absolute tolerances (Sec. 4.1.3, Eq. eta): for each
+ * component i of the C cells y [C x n] (row-major), the typical value is
+ *   ytilde_i = (min_c y_ci + max_c y_ci) / 2
+ * over the whole batch, and atol_i = eta * ytilde_i.  Where the typical
+ * value is not a positive finite number (a component that is zero or
+ * negative everywhere, or NaN in some cell), it takes the paper's default
+ * ytilde_i = 1.  Evaluated as eta * (0.5 * (min + max)). */
+EXPORT void orc_typical_atol(const double *y, long C, int n, double eta, double *atol)
+{
+    for (int i = 0; i < n; ++i) {
+        double mn = 0.0, mx = 0.0;
+        int nan = 0;
+        for (long c = 0; c < C; ++c) {
+            const double v = y[c * n + i];
+            if (v != v) { nan = 1; continue; }
+            if (c == 0 || v < mn) mn = v;
+            if (c == 0 || v > mx) mx = v;
+        }
+        double yt = 0.5 * (mn + mx);
+        if (nan || C < 1 || !(yt > 0.0) || !(yt <= 1.7976931348623157e308)) yt = 1.0;
+        atol[i] = eta * yt;
+    }
+}
+
 EXPORT void orc_bdf_l(int q, const double *xi, double *l)
 {
     l[0] = 1.0;
