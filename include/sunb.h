@@ -124,6 +124,22 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out);
  * means atol_scalar for every component.  Default: 1e-6 and 1e-10. */
 int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const double *host_atol);
 
+/* Typical-value absolute tolerances (Sec. 4.1.3, Eq. eta): from the state
+ * dev_y (the layout of sunb_integrate) the library reduces, on the
+ * context's stream, each component's minimum and maximum over the batch
+ * (for SUNB_MIXED: the mechanism components over the mechanism cells, the
+ * cosmology component over the cosmology cells) and sets
+ *   atol_i = eta * (min_i + max_i) / 2
+ * with rtol, as sunb_set_tolerances would.  Where (min + max)/2 is not a
+ * positive finite number (a component zero or negative everywhere, NaN in
+ * some cell) the typical value is the paper's default 1.  host_atol_out
+ * (nullable) receives the N (N + 1 for SUNB_MIXED) tolerances.  The
+ * paper resets typical values at user-chosen intervals: call this between
+ * outer steps as often as wanted.  Synchronises the stream (the tolerances
+ * come back to the host).  SUNB_ILL_INPUT for NULL y or eta <= 0. */
+int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol, double eta,
+                                double *host_atol_out);
+
 /* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
  * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
  * cells' pressures).  The pointer is kept, not copied: it must stay valid

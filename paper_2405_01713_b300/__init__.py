@@ -72,6 +72,7 @@ SIGNATURES = {
     "sunb_create": (ctypes.c_int, [ctypes.POINTER(_Problem), _vp, ctypes.POINTER(_vp)]),
     "sunb_set_tolerances": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp]),
     "sunb_set_params": (ctypes.c_int, [_vp, _vp]),
+    "sunb_set_typical_tolerances": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _dp]),
     "sunb_integrate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "sunb_integrate_host": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_double, _ip]),
     "sunb_get_totals": (ctypes.c_int, [_vp, ctypes.POINTER(_Totals), _vp]),
@@ -184,6 +185,16 @@ class Integrator:
         else:
             a = _cont(atol, np.float64)
             _check(lib().sunb_set_tolerances(self.ctx, rtol, 0.0, a.ctypes.data_as(_dp)), self.ctx)
+
+    def set_typical_tolerances(self, y, rtol, eta=1e-10):
+        """atol_i = eta (min + max)/2 of each component of the float64 CUDA
+        state y over the batch (Sec. 4.1.3, Eq. eta), with rtol; returns the
+        tolerances (numpy)."""
+        n = self.n_vars + (1 if self.kind == MIXED else 0)
+        out = np.empty(n)
+        _check(lib().sunb_set_typical_tolerances(self.ctx, _ptr(y), rtol, eta, out.ctypes.data_as(_dp)),
+               self.ctx)
+        return out
 
     def set_params(self, params):
         """params: float64 CUDA tensor in the kind's layout (kept alive here)."""

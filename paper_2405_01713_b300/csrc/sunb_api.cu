@@ -518,6 +518,41 @@ __global__ void exp_check_kernel(const double *x, double *y, long long n)
         y[i] = fexp(x[i], g_exp_tab);
 }
 
+// Typical values (Sec. 4.1.3): per component the minimum and maximum over
+// the cells, as order-preserving 64-bit keys (sign-magnitude flipped to
+// two's order) so that the atomics are exact and order-independent.
+__device__ __forceinline__ unsigned long long order_key(double v)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(v);
+    return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
+
+// block (x, i): component i of cells x, x + gridDim.x, ... of y [C, n]
+// (comp0 + i indexes keys: minima at [k], maxima at [KEYS_MAX + k])
+constexpr int KEYS_MAX = 128;
+__global__ void __launch_bounds__(256) typical_minmax_kernel(const double *y, long long C, int n, int comp0,
+                                                             unsigned long long *keys)
+{
+    const int i = blockIdx.y;
+    unsigned long long mn = ~0ull, mx = 0ull;
+    for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < C;
+         c += (long long)gridDim.x * blockDim.x) {
+        const unsigned long long k = order_key(y[c * n + i]);
+        mn = k < mn ? k : mn;
+        mx = k > mx ? k : mx;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long a = __shfl_xor_sync(0xffffffffu, mn, o);
+        const unsigned long long b = __shfl_xor_sync(0xffffffffu, mx, o);
+        mn = a < mn ? a : mn;
+        mx = b > mx ? b : mx;
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(keys + comp0 + i, mn);
+        atomicMax(keys + KEYS_MAX + comp0 + i, mx);
+    }
+}
+
 // One kernel launch of an outer step.
 struct LaunchSpec {
     void *func = nullptr;
@@ -553,6 +588,7 @@ struct sunb_ctx {
     // workspace
     int32_t *d_stats = nullptr;
     unsigned long long *d_queue = nullptr;
+    unsigned long long *d_minmax = nullptr;   // typical-value keys (2 x KEYS_MAX)
     DevTotals *d_totals = nullptr;
     double *d_ybuf = nullptr;
     int32_t *d_sbuf = nullptr;
@@ -1150,6 +1186,7 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
     const long long ncell = ctx->C + ctx->Cc;
     if (cudaMalloc(&ctx->d_stats, 32 * (size_t)ncell) != cudaSuccess ||
         cudaMalloc(&ctx->d_queue, 64) != cudaSuccess ||
+        cudaMalloc(&ctx->d_minmax, 16 * KEYS_MAX) != cudaSuccess ||
         cudaMalloc(&ctx->d_totals, sizeof(DevTotals)) != cudaSuccess) {
         fail(ctx, SUNB_MEM_FAIL, "cudaMalloc workspace");
         return bail(SUNB_MEM_FAIL);
@@ -1197,6 +1234,7 @@ int sunb_destroy(sunb_ctx *ctx)
     cudaFree(ctx->d_cool);
     cudaFree(ctx->d_stats);
     cudaFree(ctx->d_queue);
+    cudaFree(ctx->d_minmax);
     cudaFree(ctx->d_totals);
     cudaFree(ctx->d_ybuf);
     cudaFree(ctx->d_sbuf);
@@ -1227,6 +1265,54 @@ int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const do
         CU(cudaStreamSynchronize(ctx->stream));
     }
     return SUNB_SUCCESS;
+}
+
+int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol, double eta,
+                                double *host_atol_out)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!dev_y) return fail(ctx, SUNB_ILL_INPUT, "y is NULL");
+    if (!(eta > 0.0) || !std::isfinite(eta)) return fail(ctx, SUNB_ILL_INPUT, "eta must be positive and finite");
+    const int nc = (int)ctx->atol.size();
+    if (nc > KEYS_MAX) return fail(ctx, SUNB_ILL_INPUT, "too many components for typical values");
+    CU(cudaMemsetAsync(ctx->d_minmax, 0xff, 8 * KEYS_MAX, ctx->stream));
+    CU(cudaMemsetAsync(ctx->d_minmax + KEYS_MAX, 0, 8 * KEYS_MAX, ctx->stream));
+    auto reduce = [&](const double *y, long long C, int n, int comp0) -> int {
+        if (C <= 0) return SUNB_SUCCESS;
+        const int gx = (int)std::min<long long>((C + 255) / 256, 4LL * ctx->num_sms);
+        typical_minmax_kernel<<<dim3(gx, n), 256, 0, ctx->stream>>>(y, C, n, comp0, ctx->d_minmax);
+        CU(cudaGetLastError());
+        ctx->launches++;
+        return SUNB_SUCCESS;
+    };
+    int rc;
+    if (ctx->kind == SUNB_MIXED) {   // cosmology cells first in y, then the mechanism cells
+        if ((rc = reduce(dev_y + ctx->Cc, ctx->C, ctx->N, 0)) != SUNB_SUCCESS) return rc;
+        if ((rc = reduce(dev_y, ctx->Cc, 1, ctx->N)) != SUNB_SUCCESS) return rc;
+    } else {
+        if ((rc = reduce(dev_y, ctx->C, ctx->N, 0)) != SUNB_SUCCESS) return rc;
+    }
+    unsigned long long keys[2 * KEYS_MAX];
+    CU(cudaMemcpyAsync(keys, ctx->d_minmax, sizeof(keys), cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
+    const long long cells[2] = {ctx->C, ctx->Cc};
+    std::vector<double> atol(nc);
+    for (int i = 0; i < nc; ++i) {
+        const long long C = (ctx->kind == SUNB_MIXED && i == ctx->N) ? cells[1] : cells[0];
+        auto value = [](unsigned long long k) {
+            const unsigned long long b = (k >> 63) ? (k & 0x7fffffffffffffffull) : ~k;
+            double v;
+            std::memcpy(&v, &b, 8);
+            return v;
+        };
+        const double mn = value(keys[i]), mx = value(keys[KEYS_MAX + i]);
+        double yt = 0.5 * (mn + mx);
+        if (C < 1 || std::isnan(mn) || std::isnan(mx) || !(yt > 0.0) || !(yt <= 1.7976931348623157e308))
+            yt = 1.0;                          // the paper's default typical value
+        atol[i] = eta * yt;
+    }
+    if (host_atol_out) std::memcpy(host_atol_out, atol.data(), 8 * nc);
+    return sunb_set_tolerances(ctx, rtol, 0.0, atol.data());
 }
 
 int sunb_set_params(sunb_ctx *ctx, const double *dev_params)

@@ -211,3 +211,45 @@ def test_rhs_logarithm_against_log():
     assert torch.equal(y[~normal & ~torch.isnan(ref)], ref[~normal & ~torch.isnan(ref)])
     nan = m.log_check(torch.tensor([float("nan"), -2.0], dtype=torch.float64, device="cuda"))
     assert torch.isnan(nan).all()
+
+
+def test_typical_value_tolerances_match_the_oracle():
+    """Typical values (Sec. 4.1.3, Eq. eta) reduced on the GPU equal the
+    oracle's, bit for bit (minima and maxima are exact), for a mechanism
+    batch with negative and all-zero components, a mixed batch, and a
+    cosmology batch; integrating with them matches the oracle run with the
+    same tolerances."""
+    need_gpu()
+    m = sb()
+    w = synth.workloads.mech22(3001)
+    y0 = w["y0"].copy()
+    y0[:7, 3] = -1e-4                      # a few slightly negative mass fractions
+    y0[:, 5] = 0.0                         # a species absent everywhere: default typical value
+    it = m.from_workload(w, precision=1, lanes_per_cell=8)
+    it.set_params(dev(w["params"]))
+    yt = dev(y0)
+    a = it.set_typical_tolerances(yt, 1e-6, eta=1e-9)
+    np.testing.assert_array_equal(a, oracle.typical_atol(y0, 1e-9))
+    assert a[5] == 1e-9
+    # integrate the unmodified batch with its typical tolerances on both sides
+    y = dev(w["y0"])
+    a = it.set_typical_tolerances(y, 1e-6, eta=1e-10)
+    it.integrate(y, w["t0"], w["tout"])
+    assert it.totals()["worst_status"] == 0
+    pb = oracle.problem_from_workload(w, cells=np.arange(200))
+    yo, _, _, _ = oracle.integrate(pb, w["y0"][:200], w["t0"], w["tout"], 1e-6, a)
+    ytr, _, _, _ = oracle.integrate(pb, w["y0"][:200], w["t0"], w["tout"], 1e-12, a * 1e-4)
+    eg = np.abs(y.cpu().numpy()[:200] - ytr) / (1e-6 * np.abs(ytr) + a)
+    eo = np.abs(yo - ytr) / (1e-6 * np.abs(ytr) + a)
+    assert np.median(eg) <= 3 * np.median(eo) + 1.0 and eg.max() <= 10 * eo.max() + 100
+    # mixed: mechanism components over the mechanism cells, cosmology over its own
+    wm = synth.workloads.mixed(n_cosmo=500, n_mech=60)
+    itm = m.from_workload(wm)
+    Y = np.concatenate([wm["e0"].ravel(), wm["y0_mech"].ravel()])
+    am = itm.set_typical_tolerances(dev(Y), 1e-6, eta=1e-10)
+    np.testing.assert_array_equal(am[:-1], oracle.typical_atol(wm["y0_mech"], 1e-10))
+    assert am[-1] == oracle.typical_atol(wm["e0"], 1e-10)[0]
+    wc = synth.workloads.cosmology(777)
+    itc = m.from_workload(wc)
+    ac = itc.set_typical_tolerances(dev(wc["y0"]), 1e-6, eta=1e-10)
+    np.testing.assert_array_equal(ac, oracle.typical_atol(wc["y0"], 1e-10))
