@@ -199,6 +199,7 @@ def barrier(world):
 
 LANES_OVERRIDE = 0
 TYPICAL_ETA = None   # typical-value absolute tolerances (Sec. 4.1.3, Eq. eta) from y0, if set
+JACOBIAN_DQ = False  # difference-quotient Newton matrices (approaches 3A/3B) instead of analytic
 FORMS = {
     "plain": dict(precision=0, lanes_per_cell=32, schedule=1),
     "chosen": dict(precision=1, lanes_per_cell=0, schedule=0),
@@ -257,6 +258,8 @@ def time_form(w, form, steps, warmup, flush, world=1):
     it.set_params(p)
     if TYPICAL_ETA is not None:
         it.set_typical_tolerances(y0, w["rtol"], TYPICAL_ETA)
+    if JACOBIAN_DQ and w["kind"] in ("mechanism", "mixed") and not adjoint:
+        it.set_jacobian(1)
     kev = []        # events around the integrator launch alone (the dominant kernel)
 
     def one_step(timed=False):
@@ -313,6 +316,8 @@ def time_e2e(w, form, steps, warmup):
     it.set_params(p)
     if TYPICAL_ETA is not None:
         it.set_typical_tolerances(torch.tensor(Y, device="cuda"), w["rtol"], TYPICAL_ETA)
+    if JACOBIAN_DQ and w["kind"] in ("mechanism", "mixed"):
+        it.set_jacobian(1)
     host = torch.empty(Y.size, dtype=torch.float64, pin_memory=True).numpy()
     for _ in range(warmup):
         host[:] = Y
@@ -385,10 +390,14 @@ def main():
     ap.add_argument("--typical-eta", type=float, default=None,
                     help="typical-value absolute tolerances eta (min+max)/2 from y0 (Sec. 4.1.3) "
                          "instead of atol 1e-10 (not the benchmark configuration)")
+    ap.add_argument("--jacobian", default="analytic", choices=["analytic", "dq"],
+                    help="Newton-matrix Jacobian of mechanism cells (dq: difference quotients; "
+                         "not the benchmark configuration)")
     args = ap.parse_args()
-    global LANES_OVERRIDE, TYPICAL_ETA
+    global LANES_OVERRIDE, TYPICAL_ETA, JACOBIAN_DQ
     LANES_OVERRIDE = args.lanes
     TYPICAL_ETA = args.typical_eta
+    JACOBIAN_DQ = args.jacobian == "dq"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -468,6 +477,7 @@ def main():
             "dtype": "f64", "data": "synthetic",
             "config": {"workload": workload_name, "rtol": 1e-6,
                        "atol": 1e-10 if TYPICAL_ETA is None else f"typical values, eta {TYPICAL_ETA:g}",
+                       "jacobian": "difference quotients" if JACOBIAN_DQ else "analytic",
                        "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
                        "mapping": res["mapping"][:3] if res["mapping"] else None,
                        "l2": "flushed between steps (512 MiB write)"},

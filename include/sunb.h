@@ -140,6 +140,15 @@ int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const do
 int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol, double eta,
                                 double *host_atol_out);
 
+/* Newton-matrix Jacobian of mechanism cells: mode 0 analytic (default,
+ * Table 1 approach 2A), mode 1 forward difference quotients (approaches
+ * 3A/3B, Sec. 4.1.4): column j from f(y + inc e_j) with inc =
+ * max(sqrt(eps) |y_j|, sqrt(eps)/w_j), N right-hand sides per matrix build.
+ * Takes effect at the next sunb_integrate.  SUNB_ILL_INPUT for other modes,
+ * for kinds without mechanism cells, and with adjoint tapes (the adjoint
+ * differentiates the analytic Jacobian). */
+int sunb_set_jacobian(sunb_ctx *ctx, int mode);
+
 /* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
  * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
  * cells' pressures).  The pointer is kept, not copied: it must stay valid

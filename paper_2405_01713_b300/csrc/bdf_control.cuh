@@ -295,6 +295,7 @@ struct CellRun {
         while (phase == PH_NEWTON) {
             const int ok = c.newton_f(setup_now != 0, gamma);
             s.nfe++;
+            if (setup_now) s.nfe += c.f_per_setup();
             if (setup_now) { have_M = ok; setup_now = 0; }
             bool done = false;
             conv = 0;

@@ -253,6 +253,7 @@ struct GroupCell {
     double *dqdT, *uq;                                  // [M] gamma dq_j/dT, gamma sum_m C_m dq_j/dC_m
     double *yg;
     int *jac_lock = nullptr;   // non-null: dq/dqdT/uq shared with the other groups of the warp
+    bool jac_dq = false;       // Newton matrix from difference quotients instead of the analytic J
     // discrete-adjoint recording (null tape: no recording)
     double *tape = nullptr;
     int tape_cap = 0, rec_count = 0;
@@ -571,10 +572,12 @@ struct GroupCell {
     // f(y) of slot sin into slot sout; with jac also M = I - gamma J(y) (or
     // -gamma J without the identity) into mat.  jac is uniform over the
     // group; groups of a warp with and without it share the f part.
-    __device__ int eval(int sin, int sout, double gamma, bool jac, bool add_identity = true)
+    __device__ __forceinline__ int eval(int sin, int sout, double gamma, bool jac, bool add_identity = true)
     {
-        const double *y = V(sin);
-        double *f = V(sout);
+        return eval_p(V(sin), V(sout), gamma, jac, add_identity);
+    }
+    __device__ int eval_p(const double *y, double *f, double gamma, bool jac, bool add_identity = true)
+    {
         const double T = y[K];
         const double lnT = flog(T), invT = rcp(T);
         double s = 0.0;
@@ -758,10 +761,46 @@ struct GroupCell {
     // the right-hand-side work.
     __device__ __forceinline__ int newton_f(bool setup, double gamma)
     {
+        if (setup && jac_dq) {
+            eval(V_Y, V_F, gamma, false);
+            setup_dq(gamma);
+            release_setup();
+            return factor();
+        }
         eval(V_Y, V_F, gamma, setup);
         if (!setup) return 1;
         release_setup();                 // the matrix is assembled: scratch free
         return factor();
+    }
+    // right-hand sides a matrix build costs on top of the Newton iteration's
+    __device__ __forceinline__ int f_per_setup() const { return jac_dq ? N : 0; }
+
+    // M = I - gamma J with J by forward difference quotients (solution
+    // approaches 3A/3B of Table 1, Sec. 4.1.4): column j from
+    // f(y + inc e_j), inc = max(sqrt(eps) |y_j|, sqrt(eps) / w_j) rounded to
+    // the representable step; f(y) is the Newton iteration's (in V_F).  The
+    // perturbed f goes to the Newton-matrix scratch, which a difference-
+    // quotient build does not otherwise need.  Out of line: N right-hand
+    // sides per build.
+    __device__ __noinline__ void setup_dq(double gamma)
+    {
+        double *fp = reinterpret_cast<double *>(dq);
+        const double *y = V(V_Y), *f0 = V(V_F), *w = V(V_W);
+        double *yp = V(V_DEL);
+        const double se = 1.4901161193847656e-08;          // sqrt(DBL_EPSILON) = 2^-26
+        for (int j = 0; j < N; ++j) {
+            for (int i = g.lane; i < N; i += L) yp[i] = y[i];
+            const double yj = y[j];
+            const double inc0 = fmax(se * fabs(yj), se / w[j]);
+            const double ypj = yj + inc0, inc = ypj - yj;
+            g.sync();
+            if (g.lane == 0) yp[j] = ypj;
+            g.sync();
+            eval_p(yp, fp, 0.0, false);
+            for (int i = g.lane; i < N; i += L)
+                mat[i * N + j] = (MT)((i == j ? 1.0 : 0.0) - gamma * ((fp[i] - f0[i]) / inc));
+            g.sync();
+        }
     }
 
     __device__ int factor() { return lu_factor<L, MT>(g, mat, N, perm, dinv, nullptr); }

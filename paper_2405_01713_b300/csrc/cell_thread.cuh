@@ -278,6 +278,7 @@ struct ThreadCell {
         return s * (1.0 / N);
     }
     __device__ __forceinline__ bool acquire_setup() { return true; }
+    __device__ __forceinline__ int f_per_setup() const { return 0; }
     // the f evaluation of a Newton iteration, f(y) into V_F; with setup also
     // the Newton matrix at y, factored (0: singular)
     __device__ __forceinline__ int newton_f(bool setup, double gamma)

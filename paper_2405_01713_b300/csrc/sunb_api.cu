@@ -48,6 +48,7 @@ struct MechArgs {
     int tape_cap;
     // Newton-matrix scratch shared per warp (mech_kernel; dq_off < 0: in the cell)
     int dq_off, dq_bytes, lock_off;
+    int jac_dq;                  // 1: difference-quotient Newton matrix
 };
 
 template <int L>
@@ -91,6 +92,7 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
         const int w = threadIdx.x >> 5;
         c.set_jac_scratch(smem + a.dq_off + w * a.dq_bytes, L < 32 ? locks + w : nullptr);
     }
+    c.jac_dq = a.jac_dq != 0;
 
     const unsigned wmask = launched_warp_mask();
     long long next = (long long)blockIdx.x * a.cells_per_cta + gid;
@@ -585,6 +587,7 @@ struct sunb_ctx {
     double *d_cool = nullptr;
     int nknots = 0;
     double gamma_heat = 0.0;
+    int jac_dq = 0;                  // mechanism Newton matrix: 0 analytic, 1 difference quotients
     // workspace
     int32_t *d_stats = nullptr;
     unsigned long long *d_queue = nullptr;
@@ -849,6 +852,7 @@ static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int3
     a.tape_stride = ctx->tape_stride;
     a.tape_cap = ctx->tape_cap;
     const MechSmem ms = mech_smem(ctx, ctx->cells_per_cta, ctx->L);
+    a.jac_dq = ctx->jac_dq;
     a.dq_off = ms.dq_off;
     a.dq_bytes = ms.dq_bytes;
     a.lock_off = ms.lock_off;
@@ -1264,6 +1268,18 @@ int sunb_set_tolerances(sunb_ctx *ctx, double rtol, double atol_scalar, const do
         CU(cudaMemcpyAsync(ctx->d_tab + ctx->off.atol, at, 8 * ctx->off.N, cudaMemcpyHostToDevice, ctx->stream));
         CU(cudaStreamSynchronize(ctx->stream));
     }
+    return SUNB_SUCCESS;
+}
+
+int sunb_set_jacobian(sunb_ctx *ctx, int mode)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (mode != 0 && mode != 1) return fail(ctx, SUNB_ILL_INPUT, "jacobian mode must be 0 or 1");
+    if (mode == 1 && ctx->kind != SUNB_MECHANISM && ctx->kind != SUNB_MIXED)
+        return fail(ctx, SUNB_ILL_INPUT, "difference-quotient Jacobians are for mechanism cells");
+    if (mode == 1 && ctx->d_tape)
+        return fail(ctx, SUNB_ILL_INPUT, "the adjoint needs the analytic Jacobian");
+    ctx->jac_dq = mode;
     return SUNB_SUCCESS;
 }
 

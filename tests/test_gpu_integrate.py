@@ -268,3 +268,33 @@ def test_host_entry_point_matches_device_entry_point():
     worst = it.integrate_host(yh, 0.0, w["tout"], st)
     assert worst == 0 and np.all(st == 0)
     np.testing.assert_array_equal(yh, yd)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_difference_quotient_jacobian_matches_the_oracle(precision):
+    """Forward-difference Newton matrices (approaches 3A/3B, Sec. 4.1.4) on
+    the GPU give the method's accuracy against the oracle run with its own
+    difference-quotient Jacobian, and cost N extra right-hand sides per
+    build."""
+    need_gpu()
+    m = sb()
+    w = synth.workloads.mech22(97)
+    it = m.from_workload(w, precision=precision, lanes_per_cell=8, max_steps=20000)
+    it.set_jacobian(m.JAC_DQ)
+    it.set_params(dev(w["params"]))
+    y = dev(w["y0"])
+    it.integrate(y, w["t0"], w["tout"])
+    tot = it.totals()
+    assert tot["worst_status"] == 0
+    N = w["mech"].n_vars
+    # every f: one per Newton iteration, two per starting step, N per build
+    assert tot["nfe"] >= tot["nni"] + N * tot["nje"] + 2 * 97
+    pb = oracle.problem_from_workload(w)
+    ym, _, _, _ = oracle.integrate(pb, w["y0"], w["t0"], w["tout"], RTOL, ATOL, jac_mode=1)
+    yt, _, _, _ = oracle.integrate(pb, w["y0"], w["t0"], w["tout"], 1e-12, 1e-14)
+    _assert_matches_method(y.cpu().numpy(), ym, yt)
+    with pytest.raises(m.SunbError):
+        it.set_jacobian(7)
+    wr = synth.workloads.robertson(8)
+    with pytest.raises(m.SunbError):
+        m.from_workload(wr).set_jacobian(m.JAC_DQ)
