@@ -35,7 +35,7 @@ class Problem(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", _dp), ("max_steps", ctypes.c_int),
-                ("max_order", ctypes.c_int), ("jac_mode", ctypes.c_int)]
+                ("max_order", ctypes.c_int), ("jac_mode", ctypes.c_int), ("lin_solver", ctypes.c_int)]
 
 
 def build(force=False):
@@ -94,6 +94,8 @@ def lib():
                                         ctypes.POINTER(Options), ctypes.c_int, _dp, _dp, ctypes.c_int]
         L.orc_adjoint_sqerr.restype = ctypes.c_int
         L.orc_typical_atol.argtypes = [_dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, _dp]
+        L.orc_gmres.argtypes = [PP, ctypes.c_long, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _ip]
+        L.orc_gmres.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -175,6 +177,15 @@ def jac(pb, y, cell=0, mode=0, w=None):
     return J
 
 
+def gmres(pb, y, w, gamma, tol, b, cell=0):
+    """The inexact Newton's GMRES on (I - gamma J(y)) x = b (scaled by w,
+    J v by forward differences): (x, iterations, f evaluations)."""
+    x = _f64(b).copy()
+    nfe = np.zeros(1, dtype=np.int32)
+    k = lib().orc_gmres(pb.ref, cell, _d(_f64(y)), _d(_f64(w)), gamma, tol, _d(x), _i(nfe))
+    return x, k, int(nfe[0])
+
+
 def typical_atol(y, eta=1e-10):
     """Typical-value absolute tolerances of a batch y [C, n] (Sec. 4.1.3,
     Eq. eta): eta * (min + max)/2 per component, 1 * eta where that is not
@@ -229,7 +240,7 @@ def order_increase(z, acor, l, xi_qp1):
 
 
 def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
-              jac_mode=0, nthreads=0):
+              jac_mode=0, nthreads=0, lin_solver=0):
     """Integrate every cell of pb from t0 to tout.
 
     Returns (y, stats, hlast, worst_status); stats is a structured view with
@@ -237,7 +248,7 @@ def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
     y = _f64(y0).copy().reshape(-1, pb.n)
     C = y.shape[0]
     atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
-    o = Options(rtol, _d(atol), max_steps, max_order, jac_mode)
+    o = Options(rtol, _d(atol), max_steps, max_order, jac_mode, lin_solver)
     st = np.zeros((C, 8), dtype=np.int32)
     hl = np.zeros(C)
     worst = lib().orc_integrate(pb.ref, C, _d(y), t0, tout, ctypes.byref(o), _i(st), _d(hl), nthreads)

@@ -275,6 +275,94 @@ static double eta_from(double dsm, int p, double bias)
     return 1.0 / (pow(bias * dsm, 1.0 / (p + 1)) + 1e-6);
 }
 
+/* The linear solve of the inexact Newton iteration (solution approaches
+ * 1A/1B of Table 1; Eqs. linear and stop_linear, Sec. 2): GMRES on the
+ * system scaled by S = diag(w) and unpreconditioned,
+ *   (S M S^-1) xt = S b,  x = S^-1 xt,  M v = v - gamma J v,
+ * with J v by a forward difference along v at the current iterate y,
+ *   J v = (f(y + sig v) - f(y)) / sig,  sig = 1 / ||v||_wrms.
+ * Modified Gram-Schmidt, Givens rotations; the residual norm is |g_{k+1}|
+ * from the rotations.  Stops when it is at most tol (the 2-norm of the
+ * scaled residual) or after maxl = min(n, GMRES_MAXL) iterations (no
+ * restarts: the Krylov space may grow to the whole system), returning the
+ * approximation so far (x = 0 when ||S b|| <= tol).  b is overwritten by x.
+ * Counts its f evaluations in *nfe; returns the iterations taken. */
+#define GMRES_MAXL 64
+static int gmres_solve(const orc_problem *pb, long cell, const double *y, const double *fy,
+                       const double *w, double gamma, double tol, double *b, int32_t *nfe)
+{
+    const int n = pb->n, maxl = n < GMRES_MAXL ? n : GMRES_MAXL;
+    double V[(maxl + 1) * n], H[(maxl + 1) * maxl], cs[maxl], sn[maxl];
+    double g[maxl + 1], c[maxl], u[n], yt[n], ft[n];
+    double beta = 0.0;
+    for (int i = 0; i < n; ++i) { V[i] = w[i] * b[i]; beta += V[i] * V[i]; }
+    beta = sqrt(beta);
+    for (int i = 0; i < n; ++i) b[i] = 0.0;
+    if (!(beta > tol)) return 0;
+    for (int i = 0; i < n; ++i) V[i] /= beta;
+    g[0] = beta;
+    int k = 0;
+    for (int j = 0; j < maxl; ++j) {
+        double *vj = V + j * n, *vn = V + (j + 1) * n;
+        /* S M S^-1 v_j */
+        double nu2 = 0.0;
+        for (int i = 0; i < n; ++i) { u[i] = vj[i] / w[i]; nu2 += (u[i] * w[i]) * (u[i] * w[i]); }
+        const double sig = 1.0 / sqrt(nu2 / n);
+        for (int i = 0; i < n; ++i) yt[i] = y[i] + sig * u[i];
+        rhs_r(pb, cell, yt, ft);
+        (*nfe)++;
+        for (int i = 0; i < n; ++i) vn[i] = w[i] * (u[i] - gamma * ((ft[i] - fy[i]) / sig));
+        /* modified Gram-Schmidt */
+        for (int m = 0; m <= j; ++m) {
+            double h = 0.0;
+            for (int i = 0; i < n; ++i) h += vn[i] * V[m * n + i];
+            H[m * maxl + j] = h;
+            for (int i = 0; i < n; ++i) vn[i] -= h * V[m * n + i];
+        }
+        double hn = 0.0;
+        for (int i = 0; i < n; ++i) hn += vn[i] * vn[i];
+        hn = sqrt(hn);
+        H[(j + 1) * maxl + j] = hn;
+        /* previous rotations on column j, then the one that zeroes H[j+1][j] */
+        for (int m = 0; m < j; ++m) {
+            const double a = H[m * maxl + j], bb = H[(m + 1) * maxl + j];
+            H[m * maxl + j] = cs[m] * a + sn[m] * bb;
+            H[(m + 1) * maxl + j] = -sn[m] * a + cs[m] * bb;
+        }
+        const double a = H[j * maxl + j], bb = hn, r = sqrt(a * a + bb * bb);
+        cs[j] = r > 0.0 ? a / r : 1.0;
+        sn[j] = r > 0.0 ? bb / r : 0.0;
+        H[j * maxl + j] = r;
+        H[(j + 1) * maxl + j] = 0.0;
+        g[j + 1] = -sn[j] * g[j];
+        g[j] = cs[j] * g[j];
+        k = j + 1;
+        if (fabs(g[j + 1]) <= tol || !(hn > 0.0)) break;
+        for (int i = 0; i < n; ++i) vn[i] /= hn;
+    }
+    /* H(0:k, 0:k) c = g(0:k), x = S^-1 sum_m c_m v_m */
+    for (int i = k - 1; i >= 0; --i) {
+        double sacc = g[i];
+        for (int m = i + 1; m < k; ++m) sacc -= H[i * maxl + m] * c[m];
+        c[i] = sacc / H[i * maxl + i];
+    }
+    for (int i = 0; i < n; ++i) {
+        double xt = 0.0;
+        for (int m = 0; m < k; ++m) xt += c[m] * V[m * n + i];
+        b[i] = xt / w[i];
+    }
+    return k;
+}
+
+/* gmres_solve for tests: x into b, the iterations and f evaluations returned. */
+EXPORT int orc_gmres(const orc_problem *pb, long cell, const double *y, const double *w, double gamma,
+                     double tol, double *b, int32_t *nfe)
+{
+    double fy[pb->n];
+    rhs_r(pb, cell, y, fy);
+    return gmres_solve(pb, cell, y, fy, w, gamma, tol, b, nfe);
+}
+
 /* Matrix set-up: J at (t, y), M = I - gamma J, LU. Returns 0 on success. */
 static int setup_matrix(const orc_problem *pb, long cell, const double *y,
                         const double *w, int jac_mode, double gamma,
@@ -433,7 +521,9 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
             const double l1 = l[1], gamma = h / l1;
             Cq = 1.0 / (1.0 + l1 * xi[q]);
             int fresh = 0, conv = 0;
-            if (force_setup || !have_M || s.nst >= nst_lastsetup + 20 ||
+            const int krylov = op->lin_solver == 1;
+            if (krylov) { have_M = 1; fresh = 1; gamma_M = gamma; }   /* no matrix to keep */
+            else if (force_setup || !have_M || s.nst >= nst_lastsetup + 20 ||
                 fabs(gamma / gamma_M - 1.0) > 0.3) {
                 have_M = setup_matrix(pb, cell, z, w, op->jac_mode, gamma, M, piv, tmp) == 0;
                 s.nje++;
@@ -449,7 +539,14 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
                     rhs_r(pb, cell, ycur, f);
                     s.nfe++; s.nni++;
                     for (int i = 0; i < n; ++i) del[i] = (h * f[i] - z[n + i]) / l1 - acor[i];
-                    orc_lu_solve(n, M, piv, del);
+                    if (krylov) {
+                        /* Eq. stop_linear: c_l = 0.05 of the Newton tolerance 0.1/C_q,
+                         * a WRMS bound, i.e. sqrt(n) times it in the scaled 2-norm */
+                        gmres_solve(pb, cell, ycur, f, w, gamma, 0.05 * (0.1 / Cq) * sqrt((double)n),
+                                    del, &s.nfe);
+                    } else {
+                        orc_lu_solve(n, M, piv, del);
+                    }
                     if (gamma != gamma_M) {
                         double c = 2.0 / (1.0 + gamma / gamma_M);
                         for (int i = 0; i < n; ++i) del[i] *= c;

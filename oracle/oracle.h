@@ -48,6 +48,7 @@ typedef struct {
     int max_steps;
     int max_order;       /* 1..5 */
     int jac_mode;        /* 0: complex step, 1: forward difference */
+    int lin_solver;      /* 0: dense LU (modified Newton), 1: GMRES (inexact Newton) */
 } orc_options;
 
 /* per-cell counters, in this order */
