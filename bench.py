@@ -70,12 +70,16 @@ def jac_extra_flops(mech):
 TRAFFIC_BYTES_PER_CELL = {"mech22": 4639.7}
 
 
-def work_model(kind, mech, tot):
+def work_model(kind, mech, tot, krylov_cells=0):
     """Algorithmic FP64 flops of one launch from the per-cell counters:
     f evaluations, Newton-matrix builds (J + LU (2/3)N^3), Newton iterations
     (solve 2N^2 + 8N vector work) and steps (predict, correct, weights,
     norms; order 4 taken as typical).  An exponential or logarithm counts as
-    one operation."""
+    one operation.  With GMRES linear solves (krylov_cells > 0 cells) a
+    Newton iteration instead does kp Krylov products (the f evaluations
+    beyond one per iteration and two per starting step), each with 10N
+    vector work, modified Gram-Schmidt (4N per basis vector, 2N kp(kp+1) in
+    all), the final combination (3N kp) and 4N set-up."""
     if kind == "mechanism":
         N = mech.n_vars
         f_rhs = rhs_flops(mech)
@@ -89,6 +93,9 @@ def work_model(kind, mech, tot):
     q = 4
     f_step = (q * (q + 1) / 2) * N + 2 * (q + 1) * N + 3 * N + 8 * N + 120
     f_iter = 2 * N * N + 8 * N
+    if krylov_cells and tot["nni"]:
+        kp = max(0.0, (tot["nfe"] - tot["nni"] - 2 * krylov_cells) / tot["nni"])
+        f_iter = 8 * N + 4 * N + kp * 10 * N + 2 * N * kp * (kp + 1) + 3 * N * kp
     return (tot["nfe"] * f_rhs + tot["nje"] * f_setup + tot["nni"] * f_iter + tot["nst"] * f_step)
 
 
@@ -200,6 +207,7 @@ def barrier(world):
 LANES_OVERRIDE = 0
 TYPICAL_ETA = None   # typical-value absolute tolerances (Sec. 4.1.3, Eq. eta) from y0, if set
 JACOBIAN_DQ = False  # difference-quotient Newton matrices (approaches 3A/3B) instead of analytic
+LINEAR_GMRES = False  # matrix-free GMRES linear solves (approaches 1A/1B) instead of LU
 FORMS = {
     "plain": dict(precision=0, lanes_per_cell=32, schedule=1),
     "chosen": dict(precision=1, lanes_per_cell=0, schedule=0),
@@ -260,6 +268,8 @@ def time_form(w, form, steps, warmup, flush, world=1):
         it.set_typical_tolerances(y0, w["rtol"], TYPICAL_ETA)
     if JACOBIAN_DQ and w["kind"] in ("mechanism", "mixed") and not adjoint:
         it.set_jacobian(1)
+    if LINEAR_GMRES and w["kind"] in ("mechanism", "mixed") and not adjoint:
+        it.set_linear_solver(1)
     kev = []        # events around the integrator launch alone (the dominant kernel)
 
     def one_step(timed=False):
@@ -318,6 +328,8 @@ def time_e2e(w, form, steps, warmup):
         it.set_typical_tolerances(torch.tensor(Y, device="cuda"), w["rtol"], TYPICAL_ETA)
     if JACOBIAN_DQ and w["kind"] in ("mechanism", "mixed"):
         it.set_jacobian(1)
+    if LINEAR_GMRES and w["kind"] in ("mechanism", "mixed"):
+        it.set_linear_solver(1)
     host = torch.empty(Y.size, dtype=torch.float64, pin_memory=True).numpy()
     for _ in range(warmup):
         host[:] = Y
@@ -393,11 +405,15 @@ def main():
     ap.add_argument("--jacobian", default="analytic", choices=["analytic", "dq"],
                     help="Newton-matrix Jacobian of mechanism cells (dq: difference quotients; "
                          "not the benchmark configuration)")
+    ap.add_argument("--linear-solver", default="direct", choices=["direct", "gmres"],
+                    help="linear solves of mechanism cells (gmres: matrix-free inexact Newton; "
+                         "not the benchmark configuration)")
     args = ap.parse_args()
-    global LANES_OVERRIDE, TYPICAL_ETA, JACOBIAN_DQ
+    global LANES_OVERRIDE, TYPICAL_ETA, JACOBIAN_DQ, LINEAR_GMRES
     LANES_OVERRIDE = args.lanes
     TYPICAL_ETA = args.typical_eta
     JACOBIAN_DQ = args.jacobian == "dq"
+    LINEAR_GMRES = args.linear_solver == "gmres"
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -449,7 +465,8 @@ def main():
     # the counters describe the last launch (they are reset by every call)
     if w["kind"] == "mixed":
         flops = work_model("cosmology", None, res["parts"][0]) + \
-            work_model("mechanism", w["mech"], res["parts"][1])
+            work_model("mechanism", w["mech"], res["parts"][1],
+                       krylov_cells=(res["C"] - w["n_cosmo"]) if LINEAR_GMRES else 0)
     elif w["name"] == "adjoint":
         # forward + replay (taken as 2 exact Newton iterations per step) +
         # reverse sweep (one J, LU and transposed solve per step)
@@ -458,13 +475,15 @@ def main():
         per_setup = rhs_flops(mech) + jac_extra_flops(mech) + (2.0 / 3.0) * N ** 3 + 2 * N * N
         flops = work_model("mechanism", mech, t) + t["nst"] * (3 * per_setup + 12 * mech.n_reactions)
     else:
-        flops = work_model(w["kind"], w.get("mech"), res["totals"])
+        flops = work_model(w["kind"], w.get("mech"), res["totals"],
+                           krylov_cells=res["C"] if LINEAR_GMRES and w["kind"] == "mechanism" else 0)
     # the integrator launch alone, timed on its stream (for the adjoint
     # workload the step's three phases together)
     kms = ms if w["name"] == "adjoint" else statistics.mean(res["kernel_ms"])
     achieved = flops / (kms / 1e3) / 1e12
     traffic = None
-    if w["name"] in TRAFFIC_BYTES_PER_CELL:
+    # (captured for the benchmark configuration's kernel only)
+    if w["name"] in TRAFFIC_BYTES_PER_CELL and not (JACOBIAN_DQ or LINEAR_GMRES):
         traffic = TRAFFIC_BYTES_PER_CELL[w["name"]] * res["C"]
     roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
             "frac": achieved / FP64_PEAK_DERIVED, "traffic": traffic, "kernel_ms": kms,
@@ -478,6 +497,7 @@ def main():
             "config": {"workload": workload_name, "rtol": 1e-6,
                        "atol": 1e-10 if TYPICAL_ETA is None else f"typical values, eta {TYPICAL_ETA:g}",
                        "jacobian": "difference quotients" if JACOBIAN_DQ else "analytic",
+                       "linear_solver": "GMRES (matrix-free)" if LINEAR_GMRES else "direct (LU)",
                        "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
                        "mapping": res["mapping"][:3] if res["mapping"] else None,
                        "l2": "flushed between steps (512 MiB write)"},

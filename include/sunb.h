@@ -149,6 +149,30 @@ int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol,
  * differentiates the analytic Jacobian). */
 int sunb_set_jacobian(sunb_ctx *ctx, int mode);
 
+/* Linear solver of the Newton iteration of mechanism cells (SUNB_MIXED:
+ * its mechanism cells; thread-per-cell cells always use LU).
+ * SUNB_LS_DIRECT (default): LU factors of the Newton matrix M = I - gamma J,
+ * rebuilt as the modified Newton iteration asks.  SUNB_LS_GMRES: the
+ * matrix-free inexact Newton iteration of Table 1 approaches 1A/1B (Sec. 2,
+ * Eqs. linear and stop_linear): each Newton correction by GMRES on the
+ * system scaled by the error weights, unpreconditioned, Jacobian-vector
+ * products by a forward difference of f along the Krylov vector (increment
+ * 1/||v||_wrms), stopping once the scaled residual's WRMS norm is at most
+ * 0.05 of the Newton tolerance 0.1/C_q, after at most min(N, 64) iterations
+ * (no restarts).  No Newton matrix is built (nje stays 0) and every
+ * iteration costs one more right-hand side (counted in nfe).  The library
+ * allocates 8 * (resident lane groups) * ((l+1)(N+l) + 4l + 1 + 2N) bytes
+ * of device scratch (each group's share rounded up to 4 doubles),
+ * l = min(N, 64), on the first switch to GMRES, grows it when a later
+ * configuration has more resident groups, and frees it in sunb_destroy.  Takes effect at the next sunb_integrate or
+ * sunb_graph_capture.  SUNB_ILL_INPUT for other values, for kinds without
+ * mechanism cells, and with adjoint tapes (the adjoint differentiates the
+ * direct solver's iteration); SUNB_CUDA_ERROR if the scratch cannot be
+ * allocated. */
+#define SUNB_LS_DIRECT 0
+#define SUNB_LS_GMRES 1
+int sunb_set_linear_solver(sunb_ctx *ctx, int solver);
+
 /* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
  * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
  * cells' pressures).  The pointer is kept, not copied: it must stay valid

@@ -273,11 +273,16 @@ struct CellRun {
             gamma = h * il1;
             fresh = 0;
             setup_now = 0;
-            if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
-                fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX)
-                phase = PH_SETUP;
-            else
+            if constexpr (C::kKrylov) {   // matrix-free: nothing to build or keep
+                have_M = 1; fresh = 1; gamma_M = gamma;
                 start_newton(c);
+            } else {
+                if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
+                    fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX)
+                    phase = PH_SETUP;
+                else
+                    start_newton(c);
+            }
         }
         // the Newton matrix at the prediction z0: built by the first Newton
         // iteration below, whose f evaluation is at y = z0.  A backend whose
@@ -304,7 +309,10 @@ struct CellRun {
             } else {
                 s.nni++;
                 c.newton_residual(h, il1);
-                c.solve(V_DEL);
+                // backends with C::kKrylov: the inexact Newton iteration's GMRES
+                // solve, whose f evaluations count here
+                if constexpr (C::kKrylov) s.nfe += c.solve_krylov(gamma, Cq);
+                else c.solve(V_DEL);
                 const double dn2 = c.newton_update(cstale);
                 if (!(dn2 <= 1.7e308)) {
                     done = true;                             // not finite

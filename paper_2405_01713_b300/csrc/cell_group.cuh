@@ -228,14 +228,35 @@ __device__ void lu_solve_t(const Grp<L> &g, const double *mat, int N, const int3
 __host__ __device__ __forceinline__ int tape_header(int N) { return 8 + N; }
 __host__ __device__ __forceinline__ int tape_record(int N) { return N + 46; }
 
-template <int L, typename MT>
-struct GroupCell {
+// Krylov scratch of one lane group (global memory, doubles): the basis
+// [l+1][N], the Hessenberg matrix [l+1][l], the rotations cs and sn [l],
+// the rotated right side [l+1], the solution coefficients [l], and the
+// perturbed state and its f [N] each, for the Krylov dimension
+// l = min(N, KRYLOV_MAXL) (no restarts).
+constexpr int KRYLOV_MAXL = 64;
+__host__ __device__ __forceinline__ int krylov_dim(int N) { return N < KRYLOV_MAXL ? N : KRYLOV_MAXL; }
+__host__ __device__ __forceinline__ int krylov_doubles(int N)
+{
+    const int l = krylov_dim(N);
+    return ((l + 1) * N + (l + 1) * l + 4 * l + 1 + 2 * N + 3) & ~3;
+}
+
+// the GMRES scratch pointer, a member of the Krylov variant only (an empty
+// base of the direct one, which so keeps its layout)
+template <bool KRY> struct KrylovScratch {};
+template <> struct KrylovScratch<true> { double *kry = nullptr; };   // krylov_doubles(N) of this group
+
+template <int L, typename MT, bool KRY = false>
+struct GroupCell : KrylovScratch<KRY> {
     // one Newton iteration per superstep: a group that needs another
     // iteration takes it in the next superstep, at the same f call site as
     // the first iterations of the other groups of its warp
     static constexpr bool kNewtonLoop = false;
     // the starting step and the failure paths out of line (see CellRun)
     static constexpr bool kOutlineRare = true;
+    // matrix-free GMRES linear solves in the scratch kry instead of LU
+    // factors (a separate kernel, so the direct kernel carries none of it)
+    static constexpr bool kKrylov = KRY;
     Grp<L> g;
     MechTab tb;
     int N, K, M, NP;
@@ -801,6 +822,108 @@ struct GroupCell {
                 mat[i * N + j] = (MT)((i == j ? 1.0 : 0.0) - gamma * ((fp[i] - f0[i]) / inc));
             g.sync();
         }
+    }
+
+    // ---------------- matrix-free linear solver ----------------
+    // The inexact Newton iteration's linear solve (solution approaches 1A/1B
+    // of Table 1; Eqs. linear and stop_linear, Sec. 2): M x = b for the
+    // residual b in V_DEL, M = I - gamma J at the iterate y (V_Y, f(y) in
+    // V_F), by GMRES on the system scaled by S = diag(w) (V_W),
+    //   (S M S^-1) xt = S b,  x = S^-1 xt,
+    // unpreconditioned, with J v by a forward difference along v,
+    //   J v = (f(y + sig v) - f(y)) / sig,  sig = 1 / ||v||_wrms.
+    // Modified Gram-Schmidt and Givens rotations; stops once the rotated
+    // residual |g_{k+1}| (the scaled residual's 2-norm) is at most
+    // tol = 0.05 (NLS_COEF / C_q) sqrt(N) -- Eq. stop_linear's c_l = 0.05 of
+    // the Newton tolerance, a WRMS bound, in the 2-norm -- or after
+    // krylov_dim(N) iterations, and leaves x in V_DEL (0 when ||S b|| <= tol).  Returns the f evaluations it made.  The lanes own the
+    // vector elements i = lane (mod L) as everywhere else; lane 0 keeps the
+    // Hessenberg matrix and the rotations, and the lanes read the rotated
+    // residual back after a group barrier, so the exit is uniform.  Out of
+    // line: it only runs when the Krylov solver is selected.
+    __device__ __noinline__ int solve_krylov(double gamma, double Cq)
+    {
+        const double tol = 0.05 * (NLS_COEF / Cq) * sqrt((double)N);
+        const int l = krylov_dim(N);
+        double *Vb = this->kry, *H = Vb + (l + 1) * N, *cs = H + (l + 1) * l, *sn = cs + l;
+        double *gv = sn + l, *cv = gv + (l + 1), *yt = cv + l, *ft = yt + N;
+        double *b = V(V_DEL);
+        const double *y = V(V_Y), *fy = V(V_F), *w = V(V_W);
+        double acc = 0.0;
+        for (int i = g.lane; i < N; i += L) {
+            const double v = w[i] * b[i];
+            Vb[i] = v;
+            b[i] = 0.0;
+            acc += v * v;
+        }
+        const double beta = sqrt(g.sum(acc));
+        if (!(beta > tol)) { g.sync(); return 0; }
+        for (int i = g.lane; i < N; i += L) Vb[i] = Vb[i] / beta;
+        if (g.lane == 0) gv[0] = beta;
+        int k = 0, nfe = 0;
+        for (int j = 0; j < l; ++j) {
+            const double *vj = Vb + j * N;
+            double *vn = Vb + (j + 1) * N;
+            // S M S^-1 v_j: u = S^-1 v_j, sig = 1/||u||_wrms, y + sig u
+            double a2 = 0.0;
+            for (int i = g.lane; i < N; i += L) {
+                const double uw = (vj[i] / w[i]) * w[i];
+                a2 += uw * uw;
+            }
+            const double sig = 1.0 / sqrt(g.sum(a2) * invN);
+            for (int i = g.lane; i < N; i += L) yt[i] = y[i] + sig * (vj[i] / w[i]);
+            g.sync();
+            eval_p(yt, ft, 0.0, false);
+            ++nfe;
+            for (int i = g.lane; i < N; i += L)
+                vn[i] = w[i] * (vj[i] / w[i] - gamma * ((ft[i] - fy[i]) / sig));
+            // modified Gram-Schmidt against v_0 .. v_j
+            for (int m = 0; m <= j; ++m) {
+                const double *vm = Vb + m * N;
+                double hp = 0.0;
+                for (int i = g.lane; i < N; i += L) hp += vn[i] * vm[i];
+                const double h = g.sum(hp);
+                for (int i = g.lane; i < N; i += L) vn[i] -= h * vm[i];
+                if (g.lane == 0) H[m * l + j] = h;
+            }
+            double hp = 0.0;
+            for (int i = g.lane; i < N; i += L) hp += vn[i] * vn[i];
+            const double hn = sqrt(g.sum(hp));
+            if (g.lane == 0) {
+                // the earlier rotations on column j, then the one that zeroes H[j+1][j]
+                for (int m = 0; m < j; ++m) {
+                    const double a = H[m * l + j], bb = H[(m + 1) * l + j];
+                    H[m * l + j] = cs[m] * a + sn[m] * bb;
+                    H[(m + 1) * l + j] = -sn[m] * a + cs[m] * bb;
+                }
+                const double a = H[j * l + j], r = sqrt(a * a + hn * hn);
+                cs[j] = r > 0.0 ? a / r : 1.0;
+                sn[j] = r > 0.0 ? hn / r : 0.0;
+                H[j * l + j] = r;
+                gv[j + 1] = -sn[j] * gv[j];
+                gv[j] = cs[j] * gv[j];
+            }
+            g.sync();
+            k = j + 1;
+            if (fabs(gv[j + 1]) <= tol || !(hn > 0.0)) break;
+            for (int i = g.lane; i < N; i += L) vn[i] = vn[i] / hn;
+        }
+        // H[0:k][0:k] c = g[0:k] (upper triangular), x = S^-1 sum_m c_m v_m
+        if (g.lane == 0) {
+            for (int i = k - 1; i >= 0; --i) {
+                double s = gv[i];
+                for (int m = i + 1; m < k; ++m) s -= H[i * l + m] * cv[m];
+                cv[i] = s / H[i * l + i];
+            }
+        }
+        g.sync();
+        for (int i = g.lane; i < N; i += L) {
+            double xt = 0.0;
+            for (int m = 0; m < k; ++m) xt += cv[m] * Vb[m * N + i];
+            b[i] = xt / w[i];
+        }
+        g.sync();
+        return nfe;
     }
 
     __device__ int factor() { return lu_factor<L, MT>(g, mat, N, perm, dinv, nullptr); }

@@ -104,6 +104,8 @@ struct ThreadCell {
     // logic (cheap f, costly control) then stays aligned across the warp
     static constexpr bool kNewtonLoop = true;
     static constexpr bool kOutlineRare = false;
+    // linear solves with the LU factors (no Krylov variant)
+    static constexpr bool kKrylov = false;
     Prob prob;
     double v[NVEC][N];
     double M[N][N];

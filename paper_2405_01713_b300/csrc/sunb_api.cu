@@ -49,6 +49,9 @@ struct MechArgs {
     // Newton-matrix scratch shared per warp (mech_kernel; dq_off < 0: in the cell)
     int dq_off, dq_bytes, lock_off;
     int jac_dq;                  // 1: difference-quotient Newton matrix
+    // GMRES scratch, kry_stride doubles per lane group (null: direct solves)
+    double *kry;
+    int kry_stride;
 };
 
 template <int L>
@@ -68,7 +71,7 @@ __device__ __forceinline__ unsigned group_mask()
 // empty fill the kernel's tail with cosmology cells, one per thread.
 // Counters: queue[0] mechanism cells handed out, queue[1] cosmology cells
 // handed out, queue[2] mechanism cells finished (mixed launches).
-template <int L, typename MT, bool COSMO>
+template <int L, typename MT, bool COSMO, bool KRY>
 __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
 {
     extern __shared__ __align__(16) unsigned char smem[];
@@ -81,7 +84,7 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
     __syncthreads();
 
     const int gid = threadIdx.x / L;
-    GroupCell<L, MT> c;
+    GroupCell<L, MT, KRY> c;
     c.g.lane = threadIdx.x % L;
     c.g.mask = group_mask<L>();
     c.tb = mech_tab_at(smem, a.off);
@@ -93,6 +96,7 @@ __global__ void __launch_bounds__(256) mech_kernel(const MechArgs a)
         c.set_jac_scratch(smem + a.dq_off + w * a.dq_bytes, L < 32 ? locks + w : nullptr);
     }
     c.jac_dq = a.jac_dq != 0;
+    if constexpr (KRY) c.kry = a.kry + ((long long)blockIdx.x * a.cells_per_cta + gid) * a.kry_stride;
 
     const unsigned wmask = launched_warp_mask();
     long long next = (long long)blockIdx.x * a.cells_per_cta + gid;
@@ -588,6 +592,9 @@ struct sunb_ctx {
     int nknots = 0;
     double gamma_heat = 0.0;
     int jac_dq = 0;                  // mechanism Newton matrix: 0 analytic, 1 difference quotients
+    int lin_solver = 0;              // mechanism linear solves: 0 LU, 1 GMRES
+    double *d_krylov = nullptr;      // GMRES scratch, one block per resident lane group
+    size_t krylov_cap = 0;           // its size in doubles
     // workspace
     int32_t *d_stats = nullptr;
     unsigned long long *d_queue = nullptr;
@@ -762,14 +769,17 @@ static CellLayout shifted(CellLayout l, int shift)
 }
 
 template <int L, typename MT, bool COSMO>
-static void *mech_kernel_ptr() { return (void *)mech_kernel<L, MT, COSMO>; }
+static void *mech_kernel_ptr(bool krylov)
+{
+    return krylov ? (void *)mech_kernel<L, MT, COSMO, true> : (void *)mech_kernel<L, MT, COSMO, false>;
+}
 
-static void *pick_mech_kernel(int L, int precision, bool cosmo)
+static void *pick_mech_kernel(int L, int precision, bool cosmo, bool krylov)
 {
     const bool f = precision == SUNB_MIXED32;
 #define PICK(LL)                                                                                   \
-    if (L == LL) return f ? (cosmo ? mech_kernel_ptr<LL, float, true>() : mech_kernel_ptr<LL, float, false>()) \
-                          : (cosmo ? mech_kernel_ptr<LL, double, true>() : mech_kernel_ptr<LL, double, false>());
+    if (L == LL) return f ? (cosmo ? mech_kernel_ptr<LL, float, true>(krylov) : mech_kernel_ptr<LL, float, false>(krylov)) \
+                          : (cosmo ? mech_kernel_ptr<LL, double, true>(krylov) : mech_kernel_ptr<LL, double, false>(krylov));
     PICK(8) PICK(16) PICK(32)
 #undef PICK
     return nullptr;
@@ -794,6 +804,23 @@ static MechSmem mech_smem(const sunb_ctx *ctx, int c, int L)
     m.lock_off = m.dq_off + warps * m.dq_bytes;
     m.bytes = m.lock_off + align16(4 * warps);
     return m;
+}
+
+// GMRES scratch for every lane group of a mechanism launch (grid of
+// num_sms x ctas_per_sm CTAs of cells_per_cta groups), grown when a
+// configuration needs more; nothing without the Krylov solver.
+static int ensure_krylov(sunb_ctx *ctx)
+{
+    if (ctx->lin_solver != 1) return SUNB_SUCCESS;
+    const size_t need = (size_t)ctx->num_sms * ctx->ctas_per_sm * ctx->cells_per_cta * krylov_doubles(ctx->off.N);
+    if (need <= ctx->krylov_cap) return SUNB_SUCCESS;
+    CU(cudaStreamSynchronize(ctx->stream));
+    if (ctx->d_krylov) cudaFree(ctx->d_krylov);
+    ctx->d_krylov = nullptr;
+    ctx->krylov_cap = 0;
+    CU(cudaMalloc(&ctx->d_krylov, 8 * need));
+    ctx->krylov_cap = need;
+    return SUNB_SUCCESS;
 }
 
 // Cells per CTA for lanes-per-cell L: the count that keeps the most cells
@@ -825,12 +852,12 @@ static int configure_mech(sunb_ctx *ctx, int L, int force_cpc = 0)
     ctx->L = L;
     ctx->cells_per_cta = best_c;
     const int bytes = mech_smem(ctx, best_c, L).bytes;
-    void *k = pick_mech_kernel(L, ctx->precision, cosmo);
+    void *k = pick_mech_kernel(L, ctx->precision, cosmo, ctx->lin_solver == 1);
     CU(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
     int occ = 0;
     CU(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, best_c * L, bytes));
     ctx->ctas_per_sm = std::max(1, occ);
-    return SUNB_SUCCESS;
+    return ensure_krylov(ctx);
 }
 
 static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int32_t *status)
@@ -853,6 +880,8 @@ static MechArgs mech_args(sunb_ctx *ctx, double *y, double t0, double tout, int3
     a.tape_cap = ctx->tape_cap;
     const MechSmem ms = mech_smem(ctx, ctx->cells_per_cta, ctx->L);
     a.jac_dq = ctx->jac_dq;
+    a.kry = ctx->lin_solver == 1 ? ctx->d_krylov : nullptr;
+    a.kry_stride = krylov_doubles(ctx->off.N);
     a.dq_off = ms.dq_off;
     a.dq_bytes = ms.dq_bytes;
     a.lock_off = ms.lock_off;
@@ -894,7 +923,7 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
     const int threads = ctx->cells_per_cta * ctx->L;
     const int grid = ctx->num_sms * ctx->ctas_per_sm;
     CU(cudaMemsetAsync(ctx->d_queue, 0, 4 * sizeof(unsigned long long), ctx->stream));
-    void *k = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
+    void *k = pick_mech_kernel(ctx->L, ctx->precision, cosmo, ctx->lin_solver == 1);
     void *args[] = {&a};
     CU(cudaLaunchKernel(k, dim3(grid), dim3(threads), args, bytes, ctx->stream));
     ctx->launches++;
@@ -1088,7 +1117,7 @@ static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
     LaunchSpec &m = sp[0];
     m.thread = false;
     m.ma = mech_args(ctx, y, t0, tout, status);
-    m.func = pick_mech_kernel(ctx->L, ctx->precision, cosmo);
+    m.func = pick_mech_kernel(ctx->L, ctx->precision, cosmo, ctx->lin_solver == 1);
     m.smem = mech_smem(ctx, ctx->cells_per_cta, ctx->L).bytes;
     m.grid = dim3(ctx->num_sms * ctx->ctas_per_sm);
     m.block = dim3(ctx->cells_per_cta * ctx->L);
@@ -1239,6 +1268,7 @@ int sunb_destroy(sunb_ctx *ctx)
     cudaFree(ctx->d_stats);
     cudaFree(ctx->d_queue);
     cudaFree(ctx->d_minmax);
+    if (ctx->d_krylov) cudaFree(ctx->d_krylov);
     cudaFree(ctx->d_totals);
     cudaFree(ctx->d_ybuf);
     cudaFree(ctx->d_sbuf);
@@ -1281,6 +1311,22 @@ int sunb_set_jacobian(sunb_ctx *ctx, int mode)
         return fail(ctx, SUNB_ILL_INPUT, "the adjoint needs the analytic Jacobian");
     ctx->jac_dq = mode;
     return SUNB_SUCCESS;
+}
+
+int sunb_set_linear_solver(sunb_ctx *ctx, int solver)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (solver != SUNB_LS_DIRECT && solver != SUNB_LS_GMRES)
+        return fail(ctx, SUNB_ILL_INPUT, "linear solver must be SUNB_LS_DIRECT or SUNB_LS_GMRES");
+    if (solver == SUNB_LS_GMRES && ctx->kind != SUNB_MECHANISM && ctx->kind != SUNB_MIXED)
+        return fail(ctx, SUNB_ILL_INPUT, "GMRES solves are for mechanism cells");
+    if (solver == SUNB_LS_GMRES && ctx->d_tape)
+        return fail(ctx, SUNB_ILL_INPUT, "the adjoint needs the direct solver");
+    if (ctx->kind != SUNB_MECHANISM && ctx->kind != SUNB_MIXED) return SUNB_SUCCESS;   // LU, as always
+    ctx->lin_solver = solver;
+    // the other kernel variant: its shared-memory attribute and occupancy
+    // (the same mapping), then the scratch for its resident groups
+    return configure_mech(ctx, ctx->L, ctx->cells_per_cta);
 }
 
 int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol, double eta,

@@ -298,3 +298,48 @@ def test_difference_quotient_jacobian_matches_the_oracle(precision):
     wr = synth.workloads.robertson(8)
     with pytest.raises(m.SunbError):
         m.from_workload(wr).set_jacobian(m.JAC_DQ)
+
+
+@pytest.mark.parametrize("name,cells,lanes", [("mech22", 97, 8), ("mech22", 97, 32), ("mech54", 12, 16)])
+def test_gmres_linear_solver_matches_the_oracle(name, cells, lanes):
+    """The matrix-free inexact Newton iteration (GMRES, approaches 1A/1B,
+    Sec. 2) on the GPU gives the method's accuracy against the oracle run
+    with its own GMRES: no Newton matrix is built, every Newton iteration
+    costs its f plus the Krylov products, and Krylov corrections, whose
+    directions all have zero species sum, keep the mass fractions summing
+    to one."""
+    need_gpu()
+    m = sb()
+    w = getattr(synth.workloads, name)(cells)
+    it = m.from_workload(w, lanes_per_cell=lanes, max_steps=20000)
+    it.set_linear_solver(m.LS_GMRES)
+    it.set_params(dev(w["params"]))
+    y = dev(w["y0"])
+    it.integrate(y, w["t0"], w["tout"])
+    tot = it.totals()
+    assert tot["worst_status"] == 0
+    assert tot["nje"] == 0
+    # one f per Newton iteration, two per starting step, and the GMRES products
+    assert tot["nfe"] > tot["nni"] + 2 * cells
+    yg = y.cpu().numpy()
+    K = w["mech"].n_species
+    assert np.max(np.abs(yg[:, :K].sum(axis=1) - 1.0)) < 10 * RTOL
+    pb = oracle.problem_from_workload(w)
+    ym, sm, _, _ = oracle.integrate(pb, w["y0"], w["t0"], w["tout"], RTOL, ATOL, lin_solver=1)
+    yt, _, _, _ = oracle.integrate(pb, w["y0"], w["t0"], w["tout"], 1e-12, 1e-14)
+    _assert_matches_method(yg, ym, yt)
+    # and the GPU takes as many steps as the oracle, statistically
+    assert abs(tot["nst"] / cells - sm[:, 0].mean()) < 0.25 * sm[:, 0].mean()
+
+
+def test_gmres_linear_solver_rejections():
+    need_gpu()
+    m = sb()
+    w = synth.workloads.mech22(4)
+    it = m.from_workload(w)
+    with pytest.raises(m.SunbError):
+        it.set_linear_solver(2)
+    it.set_linear_solver(m.LS_GMRES)
+    it.set_linear_solver(m.LS_DIRECT)
+    with pytest.raises(m.SunbError):
+        m.from_workload(synth.workloads.robertson(8)).set_linear_solver(m.LS_GMRES)
