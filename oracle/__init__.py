@@ -35,7 +35,8 @@ class Problem(ctypes.Structure):
 
 class Options(ctypes.Structure):
     _fields_ = [("rtol", ctypes.c_double), ("atol", _dp), ("max_steps", ctypes.c_int),
-                ("max_order", ctypes.c_int), ("jac_mode", ctypes.c_int), ("lin_solver", ctypes.c_int)]
+                ("max_order", ctypes.c_int), ("jac_mode", ctypes.c_int), ("lin_solver", ctypes.c_int),
+                ("method", ctypes.c_int)]
 
 
 def build(force=False):
@@ -96,6 +97,8 @@ def lib():
         L.orc_typical_atol.argtypes = [_dp, ctypes.c_long, ctypes.c_int, ctypes.c_double, _dp]
         L.orc_gmres.argtypes = [PP, ctypes.c_long, _dp, _dp, ctypes.c_double, ctypes.c_double, _dp, _ip]
         L.orc_gmres.restype = ctypes.c_int
+        L.orc_erk_table.argtypes = [_dp, _dp, _dp]
+        L.orc_erk_fixed.argtypes = [PP, ctypes.c_long, ctypes.c_double, ctypes.c_int, _dp, _dp]
         _lib = L
     return _lib
 
@@ -186,6 +189,21 @@ def gmres(pb, y, w, gamma, tol, b, cell=0):
     return x, k, int(nfe[0])
 
 
+def erk_table():
+    """The explicit method's table: (A [5, 4], b [5], bh [5])."""
+    A, b, bh = np.empty((5, 4)), np.empty(5), np.empty(5)
+    lib().orc_erk_table(_d(A), _d(b), _d(bh))
+    return A, b, bh
+
+
+def erk_fixed(pb, y0, h, nsteps, cell=0):
+    """nsteps explicit steps of size h from y0: (y, E of the last step)."""
+    y = _f64(y0).copy()
+    E = np.empty(pb.n)
+    lib().orc_erk_fixed(pb.ref, cell, h, nsteps, _d(y), _d(E))
+    return y, E
+
+
 def typical_atol(y, eta=1e-10):
     """Typical-value absolute tolerances of a batch y [C, n] (Sec. 4.1.3,
     Eq. eta): eta * (min + max)/2 per component, 1 * eta where that is not
@@ -240,7 +258,7 @@ def order_increase(z, acor, l, xi_qp1):
 
 
 def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
-              jac_mode=0, nthreads=0, lin_solver=0):
+              jac_mode=0, nthreads=0, lin_solver=0, method=0):
     """Integrate every cell of pb from t0 to tout.
 
     Returns (y, stats, hlast, worst_status); stats is a structured view with
@@ -248,7 +266,7 @@ def integrate(pb, y0, t0, tout, rtol, atol, max_steps=100000, max_order=5,
     y = _f64(y0).copy().reshape(-1, pb.n)
     C = y.shape[0]
     atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
-    o = Options(rtol, _d(atol), max_steps, max_order, jac_mode, lin_solver)
+    o = Options(rtol, _d(atol), max_steps, max_order, jac_mode, lin_solver, method)
     st = np.zeros((C, 8), dtype=np.int32)
     hl = np.zeros(C)
     worst = lib().orc_integrate(pb.ref, C, _d(y), t0, tout, ctypes.byref(o), _i(st), _d(hl), nthreads)

@@ -685,6 +685,135 @@ done:
     return s.status;
 }
 
+/* ---- explicit Runge-Kutta (the explicit alternative of Sec. 4.1.5) -----
+ * The paper compares CVODE's implicit BDF with a fourth-order explicit,
+ * adaptive-step method of ARKODE (Sec. 2: explicit RK with step adaptivity
+ * from an embedded error estimate under the same WRMS test) and reports
+ * about five right-hand sides per step; it does not name the table.
+ * Reading: Merson's five-stage pair, order 4 with an embedded order-3
+ * solution (Merson 1957; Hairer, Norsett & Wanner, Solving ODEs I, II.4),
+ * advancing with the order-4 weights:
+ *   k_j = f(y_n + h sum_{m<j} a_jm k_m),  y_{n+1} = y_n + h sum b_j k_j,
+ *   E = h sum (b_j - bh_j) k_j,  accept iff ||E||_wrms < 1 (Eq. wrms, the
+ *   weights from y_n as in the BDF),
+ * step factor eta = 0.9 (1/||E||)^(1/4) (the embedded order 3, plus one),
+ * at most 10 after an accepted step (1e4 after the first), at least 0.1,
+ * at most 1 after a rejection and at most 0.3 from the second rejection of
+ * a step on (where f is only piecewise smooth the estimate falls more
+ * slowly than h^4); seven rejections of one step give ERR_FAILURE.  The starting step is the BDF's (an order-1 estimate, so the
+ * first accepted steps grow it); the last step lands exactly on tout; k_1 =
+ * f(y_n) is kept across a rejection.  nfe counts every f; nef the
+ * rejections; qlast is 4. */
+static const double ERK_A[5][4] = {
+    {0.0, 0.0, 0.0, 0.0},
+    {1.0 / 3.0, 0.0, 0.0, 0.0},
+    {1.0 / 6.0, 1.0 / 6.0, 0.0, 0.0},
+    {1.0 / 8.0, 0.0, 3.0 / 8.0, 0.0},
+    {1.0 / 2.0, 0.0, -3.0 / 2.0, 2.0},
+};
+static const double ERK_B[5] = {1.0 / 6.0, 0.0, 0.0, 2.0 / 3.0, 1.0 / 6.0};
+static const double ERK_BH[5] = {1.0 / 10.0, 0.0, 3.0 / 10.0, 2.0 / 5.0, 1.0 / 5.0};
+
+/* the table for tests: A [5][4], b [5], bh [5] */
+EXPORT void orc_erk_table(double *A, double *b, double *bh)
+{
+    memcpy(A, ERK_A, sizeof(ERK_A));
+    memcpy(b, ERK_B, sizeof(ERK_B));
+    memcpy(bh, ERK_BH, sizeof(ERK_BH));
+}
+
+/* One step of size h from y (k1 = f(y) given): y_new and E. */
+static void erk_step(const orc_problem *pb, long cell, const double *y, double h,
+                     double *k /* [5][n], k[0] = f(y) */, double *ys, double *ynew, double *E)
+{
+    const int n = pb->n;
+    for (int j = 1; j < 5; ++j) {
+        for (int i = 0; i < n; ++i) {
+            double s = 0.0;
+            for (int m = 0; m < j; ++m) s += ERK_A[j][m] * k[m * n + i];
+            ys[i] = y[i] + h * s;
+        }
+        rhs_r(pb, cell, ys, k + j * n);
+    }
+    for (int i = 0; i < n; ++i) {
+        double sb = 0.0, se = 0.0;
+        for (int m = 0; m < 5; ++m) {
+            sb += ERK_B[m] * k[m * n + i];
+            se += (ERK_B[m] - ERK_BH[m]) * k[m * n + i];
+        }
+        ynew[i] = y[i] + h * sb;
+        E[i] = h * se;
+    }
+}
+
+/* Fixed step size: nsteps steps of size h from y (in place); E of the last
+ * step in E_out.  Pins the order of the method and of its estimate. */
+EXPORT void orc_erk_fixed(const orc_problem *pb, long cell, double h, int nsteps, double *y, double *E_out)
+{
+    const int n = pb->n;
+    double *k = malloc(sizeof(double) * 5 * n), *ys = malloc(sizeof(double) * n);
+    double *yn = malloc(sizeof(double) * n);
+    for (int s = 0; s < nsteps; ++s) {
+        rhs_r(pb, cell, y, k);
+        erk_step(pb, cell, y, h, k, ys, yn, E_out);
+        memcpy(y, yn, sizeof(double) * n);
+    }
+    free(k); free(ys); free(yn);
+}
+
+static int erk_cell(const orc_problem *pb, long cell, double *y, double t0, double tout,
+                    const orc_options *op, orc_stats *st, double *hlast)
+{
+    const int n = pb->n;
+    double *k = malloc(sizeof(double) * 5 * n), *ys = malloc(sizeof(double) * n);
+    double *yn = malloc(sizeof(double) * n), *E = malloc(sizeof(double) * n);
+    double *w = malloc(sizeof(double) * n), *tmp = malloc(sizeof(double) * n);
+    orc_stats s = {0, 0, 0, 0, 0, 0, 4, ORC_SUCCESS};
+    double t = t0, h = 0.0, etamax = 1e4;
+    int nef = 0;
+    if (!(tout > t0)) goto done;
+    rhs_r(pb, cell, y, k);
+    s.nfe++;
+    if (!all_finite(n, k) || !all_finite(n, y)) { s.status = ORC_NONFINITE; goto done; }
+    set_weights(n, y, op->rtol, op->atol, w);
+    h = initial_step(pb, cell, t0, tout, y, k, w, ys, tmp, &s.nfe);
+    int have_k1 = 1;
+    while (t < tout) {
+        if (s.nst >= op->max_steps) { s.status = ORC_TOO_MUCH_WORK; break; }
+        int last = 0;
+        if (t + h >= tout || tout - (t + h) <= 4.0 * DBL_EPSILON * fabs(tout)) { h = tout - t; last = 1; }
+        set_weights(n, y, op->rtol, op->atol, w);
+        if (!have_k1) { rhs_r(pb, cell, y, k); s.nfe++; have_k1 = 1; }
+        erk_step(pb, cell, y, h, k, ys, yn, E);
+        s.nfe += 4;
+        const double err = wrms(n, E, w);
+        if (err < 1.0) {          /* accept */
+            memcpy(y, yn, sizeof(double) * n);
+            t = last ? tout : t + h;
+            s.nst++;
+            have_k1 = 0;
+            nef = 0;
+            if (last) break;
+            double eta = err > 0.0 ? 0.9 / sqrt(sqrt(err)) : etamax;
+            h *= fmin(eta, etamax);
+            etamax = 10.0;
+            continue;
+        }
+        s.nef++; nef++;           /* reject (a non-finite E counts as one) */
+        if (nef >= 7) { s.status = ORC_ERR_FAILURE; break; }
+        double eta = isfinite(err) ? 0.9 / sqrt(sqrt(err)) : 0.1;
+        if (nef >= 2) eta = fmin(eta, 0.3);
+        h *= fmax(0.1, eta);
+        etamax = 1.0;
+        if (t + h == t) { s.status = ORC_H_TOO_SMALL; break; }
+    }
+done:
+    if (st) *st = s;
+    if (hlast) *hlast = h;
+    free(k); free(ys); free(yn); free(E); free(w); free(tmp);
+    return s.status;
+}
+
 /* Integrate ncells independent cells from t0 to tout (Sec. 2: one ODE
  * system per cell, all over the same outer interval dt_CFD).  y is
  * [ncells, n] (cell-contiguous "CY" order, Sec. 4.1.2).  Returns the most
@@ -701,8 +830,11 @@ EXPORT int orc_integrate(const orc_problem *pb, long ncells, double *y, double t
 #endif
 #pragma omp parallel for schedule(dynamic, 4) reduction(min : worst)
     for (long c = 0; c < ncells; ++c) {
-        int r = bdf_cell(pb, c, y + (size_t)c * pb->n, t0, tout, op,
-                         stats ? stats + c : NULL, hlast ? hlast + c : NULL, NULL);
+        int r = op->method == 1
+                    ? erk_cell(pb, c, y + (size_t)c * pb->n, t0, tout, op, stats ? stats + c : NULL,
+                               hlast ? hlast + c : NULL)
+                    : bdf_cell(pb, c, y + (size_t)c * pb->n, t0, tout, op,
+                               stats ? stats + c : NULL, hlast ? hlast + c : NULL, NULL);
         if (r < worst) worst = r;
     }
     return worst;

@@ -49,6 +49,7 @@ typedef struct {
     int max_order;       /* 1..5 */
     int jac_mode;        /* 0: complex step, 1: forward difference */
     int lin_solver;      /* 0: dense LU (modified Newton), 1: GMRES (inexact Newton) */
+    int method;          /* 0: BDF (CVODE kind), 1: explicit Runge-Kutta 4(3) (ARKODE kind) */
 } orc_options;
 
 /* per-cell counters, in this order */
