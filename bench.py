@@ -70,7 +70,7 @@ def jac_extra_flops(mech):
 TRAFFIC_BYTES_PER_CELL = {"mech22": 4639.7}
 
 
-def work_model(kind, mech, tot, krylov_cells=0):
+def work_model(kind, mech, tot, krylov_cells=0, explicit=False):
     """Algorithmic FP64 flops of one launch from the per-cell counters:
     f evaluations, Newton-matrix builds (J + LU (2/3)N^3), Newton iterations
     (solve 2N^2 + 8N vector work) and steps (predict, correct, weights,
@@ -79,7 +79,10 @@ def work_model(kind, mech, tot, krylov_cells=0):
     Newton iteration instead does kp Krylov products (the f evaluations
     beyond one per iteration and two per starting step), each with 10N
     vector work, modified Gram-Schmidt (4N per basis vector, 2N kp(kp+1) in
-    all), the final combination (3N kp) and 4N set-up."""
+    all), the final combination (3N kp) and 4N set-up.  The explicit method
+    (explicit=True) has f evaluations and, per attempt (nst + nef), the
+    stage combinations (20N), the error estimate and its norm (14N), the
+    weights (3N), the update (10N) and 30 control operations."""
     if kind == "mechanism":
         N = mech.n_vars
         f_rhs = rhs_flops(mech)
@@ -90,6 +93,8 @@ def work_model(kind, mech, tot, krylov_cells=0):
     else:   # cosmology: log, 6 compares, 2 exponentials, power-law algebra
         N = 1
         f_rhs, f_setup = 20, 8
+    if explicit:
+        return tot["nfe"] * f_rhs + (tot["nst"] + tot["nef"]) * (47 * N + 30)
     q = 4
     f_step = (q * (q + 1) / 2) * N + 2 * (q + 1) * N + 3 * N + 8 * N + 120
     f_iter = 2 * N * N + 8 * N
@@ -208,6 +213,7 @@ LANES_OVERRIDE = 0
 TYPICAL_ETA = None   # typical-value absolute tolerances (Sec. 4.1.3, Eq. eta) from y0, if set
 JACOBIAN_DQ = False  # difference-quotient Newton matrices (approaches 3A/3B) instead of analytic
 LINEAR_GMRES = False  # matrix-free GMRES linear solves (approaches 1A/1B) instead of LU
+METHOD_ERK = False    # explicit Runge-Kutta 4(3) instead of the BDF (thread-per-cell workloads)
 FORMS = {
     "plain": dict(precision=0, lanes_per_cell=32, schedule=1),
     "chosen": dict(precision=1, lanes_per_cell=0, schedule=0),
@@ -270,6 +276,8 @@ def time_form(w, form, steps, warmup, flush, world=1):
         it.set_jacobian(1)
     if LINEAR_GMRES and w["kind"] in ("mechanism", "mixed") and not adjoint:
         it.set_linear_solver(1)
+    if METHOD_ERK:
+        it.set_method(1)
     kev = []        # events around the integrator launch alone (the dominant kernel)
 
     def one_step(timed=False):
@@ -330,6 +338,8 @@ def time_e2e(w, form, steps, warmup):
         it.set_jacobian(1)
     if LINEAR_GMRES and w["kind"] in ("mechanism", "mixed"):
         it.set_linear_solver(1)
+    if METHOD_ERK:
+        it.set_method(1)
     host = torch.empty(Y.size, dtype=torch.float64, pin_memory=True).numpy()
     for _ in range(warmup):
         host[:] = Y
@@ -408,12 +418,18 @@ def main():
     ap.add_argument("--linear-solver", default="direct", choices=["direct", "gmres"],
                     help="linear solves of mechanism cells (gmres: matrix-free inexact Newton; "
                          "not the benchmark configuration)")
+    ap.add_argument("--method", default="bdf", choices=["bdf", "erk"],
+                    help="integration method of thread-per-cell workloads (erk: explicit Runge-Kutta "
+                         "4(3); not the benchmark configuration)")
     args = ap.parse_args()
-    global LANES_OVERRIDE, TYPICAL_ETA, JACOBIAN_DQ, LINEAR_GMRES
+    global LANES_OVERRIDE, TYPICAL_ETA, JACOBIAN_DQ, LINEAR_GMRES, METHOD_ERK
     LANES_OVERRIDE = args.lanes
     TYPICAL_ETA = args.typical_eta
     JACOBIAN_DQ = args.jacobian == "dq"
     LINEAR_GMRES = args.linear_solver == "gmres"
+    METHOD_ERK = args.method == "erk"
+    if METHOD_ERK and args.workload not in ("cosmology", "robertson"):
+        ap.error("--method erk is for the thread-per-cell workloads (cosmology, robertson)")
 
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -476,7 +492,8 @@ def main():
         flops = work_model("mechanism", mech, t) + t["nst"] * (3 * per_setup + 12 * mech.n_reactions)
     else:
         flops = work_model(w["kind"], w.get("mech"), res["totals"],
-                           krylov_cells=res["C"] if LINEAR_GMRES and w["kind"] == "mechanism" else 0)
+                           krylov_cells=res["C"] if LINEAR_GMRES and w["kind"] == "mechanism" else 0,
+                           explicit=METHOD_ERK)
     # the integrator launch alone, timed on its stream (for the adjoint
     # workload the step's three phases together)
     kms = ms if w["name"] == "adjoint" else statistics.mean(res["kernel_ms"])
@@ -498,6 +515,7 @@ def main():
                        "atol": 1e-10 if TYPICAL_ETA is None else f"typical values, eta {TYPICAL_ETA:g}",
                        "jacobian": "difference quotients" if JACOBIAN_DQ else "analytic",
                        "linear_solver": "GMRES (matrix-free)" if LINEAR_GMRES else "direct (LU)",
+                       "method": "explicit RK 4(3)" if METHOD_ERK else "BDF",
                        "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
                        "mapping": res["mapping"][:3] if res["mapping"] else None,
                        "l2": "flushed between steps (512 MiB write)"},

@@ -173,6 +173,24 @@ int sunb_set_jacobian(sunb_ctx *ctx, int mode);
 #define SUNB_LS_GMRES 1
 int sunb_set_linear_solver(sunb_ctx *ctx, int solver);
 
+/* Integration method of thread-per-cell kinds (SUNB_ROBERTSON,
+ * SUNB_COSMOLOGY).  SUNB_METHOD_BDF (default): the variable-order BDF.
+ * SUNB_METHOD_ERK: the explicit alternative of Sec. 4.1.5, a fourth-order
+ * adaptive Runge-Kutta method: Merson's five-stage pair with an embedded
+ * third-order estimate under the same WRMS test (||E||_wrms < 1, weights
+ * from y_n), step factor 0.9 ||E||^(-1/4) within [0.1, 10] (1e4 after the
+ * first step, 1 after a rejection, 0.3 from a step's second rejection),
+ * the BDF's starting step, exact landing on tout.  Its counters: nst
+ * accepted steps, nfe every f (1 + 5 nst + 4 nef), nef rejections, nje =
+ * nni = ncf = 0, qlast = 4; seven rejections of one step give
+ * SUNB_ERR_FAILURE.  On stiff cells its step is held to the stability bound,
+ * so expect SUNB_TOO_MUCH_WORK there (the paper's finding).  Takes effect at
+ * the next sunb_integrate or sunb_graph_capture.  SUNB_ILL_INPUT for other
+ * values and for kinds with mechanism cells (not built for lane groups). */
+#define SUNB_METHOD_BDF 0
+#define SUNB_METHOD_ERK 1
+int sunb_set_method(sunb_ctx *ctx, int method);
+
 /* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
  * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
  * cells' pressures).  The pointer is kept, not copied: it must stay valid

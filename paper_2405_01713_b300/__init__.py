@@ -24,6 +24,7 @@ FP64, MIXED32 = 0, 1
 SCHED_QUEUE, SCHED_STATIC = 0, 1
 JAC_ANALYTIC, JAC_DQ = 0, 1
 LS_DIRECT, LS_GMRES = 0, 1
+METHOD_BDF, METHOD_ERK = 0, 1
 STATUS = {0: "SUCCESS", -1: "TOO_MUCH_WORK", -3: "ERR_FAILURE", -4: "CONV_FAILURE",
           -5: "H_TOO_SMALL", -6: "NONFINITE", -20: "MEM_FAIL", -22: "ILL_INPUT",
           -30: "CUDA_ERROR", -31: "NO_RECORD"}
@@ -77,6 +78,7 @@ SIGNATURES = {
     "sunb_set_typical_tolerances": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _dp]),
     "sunb_set_jacobian": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sunb_set_linear_solver": (ctypes.c_int, [_vp, ctypes.c_int]),
+    "sunb_set_method": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sunb_integrate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "sunb_integrate_host": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_double, _ip]),
     "sunb_get_totals": (ctypes.c_int, [_vp, ctypes.POINTER(_Totals), _vp]),
@@ -209,6 +211,11 @@ class Integrator:
         """LS_DIRECT (default: LU of the Newton matrix) or LS_GMRES
         (matrix-free inexact Newton) for the linear solves of mechanism cells."""
         _check(lib().sunb_set_linear_solver(self.ctx, int(solver)), self.ctx)
+
+    def set_method(self, method):
+        """METHOD_BDF (default) or METHOD_ERK (explicit Runge-Kutta 4(3))
+        for thread-per-cell kinds (Robertson, cosmology)."""
+        _check(lib().sunb_set_method(self.ctx, int(method)), self.ctx)
 
     def set_params(self, params):
         """params: float64 CUDA tensor in the kind's layout (kept alive here)."""

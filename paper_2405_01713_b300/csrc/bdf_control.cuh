@@ -121,6 +121,43 @@ __device__ __forceinline__ double eta_viable2(int p)
     return r;
 }
 
+// The first steps of a cell for the explicit controller, the same as
+// CellRun::begin_body's: y0 into V_Z0, f(t0, y0) into V_F, the weights from
+// y0, and the starting step h of Hairer, Norsett & Wanner (order 1, WRMS
+// norms), at most tout - t0.  False when the cell is finished already:
+// tout <= t0, or a non-finite y0 or f (s.status = ST_NONFINITE).  (The BDF
+// keeps its inline copy: calling this from begin_body changed the register
+// allocation of the thread-per-cell BDF kernel.)
+template <class C>
+__device__ __forceinline__ bool start_cell(C &c, const Controls &ctl, CellStats &s, double &h)
+{
+    const double t0 = ctl.t0, tout = ctl.tout;
+    c.load_y(V_Z0);
+    if (!(tout > t0)) return false;
+    c.rhs_start(V_Z0, V_F);
+    s.nfe++;
+    if (!c.all_finite(V_F) || !c.all_finite(V_Z0)) {
+        s.status = ST_NONFINITE;
+        return false;
+    }
+    c.set_weights(V_Z0, ctl.rtol);
+    const double span = tout - t0;
+    const double d0 = c.wrms2(V_Z0), d1 = c.wrms2(V_F);   // squared
+    double h0 = (d0 < 1e-10 || d1 < 1e-10) ? 1e-6 * span : 0.01 * sqrt(d0 * rcp(d1));
+    if (h0 > span) h0 = span;
+    c.axpby(V_Y, 1.0, V_Z0, h0, V_F);
+    c.rhs_start(V_Y, V_DEL);
+    s.nfe++;
+    const double rh0 = rcp(h0);
+    const double d2 = c.wrms2_lin(rh0, V_DEL, -rh0, V_F);
+    const double dm = fmax(d1, d2);
+    double h1 = (dm <= 1e-30) ? fmax(1e-6 * span, h0 * 1e-3) : sqrt(0.01 * rcp(sqrt(dm)));
+    h = fmin(100.0 * h0, h1);
+    if (!(h > 0.0)) h = 1e-6 * span;
+    h = fmin(h, span);
+    return true;
+}
+
 // The controller as a state machine that advances a cell by at most one
 // step attempt (or, for backends that ask for it, one Newton iteration) per
 // call ("superstep").  Its phases -- STEP (start a step),
@@ -504,11 +541,12 @@ __device__ void bdf_cell(C &c, const Controls &ctl, CellStats &s)
 // of its warp keeps stepping.  wmask holds the warp's launched threads; the
 // loop ends when none of them has a cell left.  bind(cell) points the
 // backend at a cell before it begins; done(cell, stats) reports it.
-template <class C, class Next, class Bind, class Done>
+// Run is the controller (CellRun, or ErkRun for the explicit method).
+template <template <class> class Run = CellRun, class C, class Next, class Bind, class Done>
 __device__ __forceinline__ void run_cells(C &c, const Controls &ctl, unsigned wmask, Next next,
                                           Bind bind, Done done)
 {
-    CellRun<C> run;
+    Run<C> run;
     run.phase = PH_DONE;
     long long cell = -1;
     for (;;) {

@@ -4,6 +4,7 @@
 // compile time; runtime indices select through predicates).
 #pragma once
 #include "sunb_common.cuh"
+#include "erk_control.cuh"
 
 namespace sunb {
 
@@ -279,6 +280,54 @@ struct ThreadCell {
         }
         return s * (1.0 / N);
     }
+    // ---------------- explicit Runge-Kutta (ErkRun) ----------------
+    // stage derivatives k_0..k_4 in slots 1..5; the stage index j is a
+    // runtime value, so slots are selected through predicates
+    __device__ __forceinline__ void erk_stage(int j, double h)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double s = 0.0;
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (m < j) s += ERK_A[j][m] * v[1 + m][i];
+            v[V_Y][i] = v[V_Z0][i] + h * s;
+        }
+    }
+    __device__ __forceinline__ void erk_rhs(int j)
+    {
+        double f[N];
+        prob.rhs(v[V_Y], f);
+#pragma unroll
+        for (int m = 0; m < 5; ++m)
+            if (m == j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[1 + m][i] = f[i];
+    }
+    __device__ __forceinline__ double erk_error2(double h) const
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double e = 0.0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) e += (ERK_B[m] - ERK_BH[m]) * v[1 + m][i];
+            const double t = (h * e) * v[V_W][i];
+            s += t * t;
+        }
+        return s * (1.0 / N);
+    }
+    __device__ __forceinline__ void erk_accept(double h)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) {
+            double sb = 0.0;
+#pragma unroll
+            for (int m = 0; m < 5; ++m) sb += ERK_B[m] * v[1 + m][i];
+            v[V_Z0][i] += h * sb;
+        }
+    }
+
     __device__ __forceinline__ bool acquire_setup() { return true; }
     __device__ __forceinline__ int f_per_setup() const { return 0; }
     // the f evaluation of a Newton iteration, f(y) into V_F; with setup also

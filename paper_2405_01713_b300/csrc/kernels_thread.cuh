@@ -9,6 +9,7 @@
 #include "sunb_common.cuh"
 #include "bdf_control.cuh"
 #include "cell_thread.cuh"
+#include "erk_control.cuh"
 
 namespace sunb {
 
@@ -86,8 +87,9 @@ struct ThreadArgs {
 // take cells from the device queue; a batch that fits in one wave
 // (spread_lanes > 0) is spread over all SMs and warps instead, cell
 // b + grid (w + W l) for lane l < spread_lanes of warp w of CTA b, so that
-// few cells do not crowd a few SMs.
-template <class Prob>
+// few cells do not crowd a few SMs.  ERK: the explicit Runge-Kutta
+// controller instead of the BDF one (a separate kernel).
+template <class Prob, bool ERK = false>
 __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 {
     __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
@@ -99,24 +101,24 @@ __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 #pragma unroll
     for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
     bool taken = false;
-    run_cells(
-        tc, a.ctl, launched_warp_mask(),
-        [&]() -> long long {
-            if (a.spread_lanes > 0) {
-                const int l = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
-                if (taken || l >= a.spread_lanes) return -1;
-                taken = true;
-                const long long cell = blockIdx.x + (long long)gridDim.x * (w + (long long)W * l);
-                return cell < a.n ? cell : -1;
-            }
-            const long long cell = grab_thread(a.queue);
+    auto next = [&]() -> long long {
+        if (a.spread_lanes > 0) {
+            const int l = threadIdx.x & 31, w = threadIdx.x >> 5, W = blockDim.x >> 5;
+            if (taken || l >= a.spread_lanes) return -1;
+            taken = true;
+            const long long cell = blockIdx.x + (long long)gridDim.x * (w + (long long)W * l);
             return cell < a.n ? cell : -1;
-        },
-        [&](long long cell) {
-            tc.prob.load(a.params, cell);
-            tc.yg = a.y + cell * Prob::N;
-        },
-        [&](long long cell, const CellStats &st) { write_stats(a.stats, a.status, cell, st); });
+        }
+        const long long cell = grab_thread(a.queue);
+        return cell < a.n ? cell : -1;
+    };
+    auto bind = [&](long long cell) {
+        tc.prob.load(a.params, cell);
+        tc.yg = a.y + cell * Prob::N;
+    };
+    auto done = [&](long long cell, const CellStats &st) { write_stats(a.stats, a.status, cell, st); };
+    if constexpr (ERK) run_cells<ErkRun>(tc, a.ctl, launched_warp_mask(), next, bind, done);
+    else run_cells(tc, a.ctl, launched_warp_mask(), next, bind, done);
 }
 
 }  // namespace sunb

@@ -593,6 +593,7 @@ struct sunb_ctx {
     double gamma_heat = 0.0;
     int jac_dq = 0;                  // mechanism Newton matrix: 0 analytic, 1 difference quotients
     int lin_solver = 0;              // mechanism linear solves: 0 LU, 1 GMRES
+    int method = 0;                  // thread-per-cell kinds: SUNB_METHOD_BDF or SUNB_METHOD_ERK
     double *d_krylov = nullptr;      // GMRES scratch, one block per resident lane group
     size_t krylov_cap = 0;           // its size in doubles
     // workspace
@@ -1077,7 +1078,9 @@ static int thread_spec(sunb_ctx *ctx, const ThreadArgs &a, bool robertson, Launc
 {
     sp.thread = true;
     sp.ta = a;
-    sp.func = robertson ? (void *)thread_kernel<RobertsonProblem> : (void *)thread_kernel<CosmologyProblem>;
+    const bool erk = ctx->method == SUNB_METHOD_ERK;
+    sp.func = robertson ? (erk ? (void *)thread_kernel<RobertsonProblem, true> : (void *)thread_kernel<RobertsonProblem>)
+                        : (erk ? (void *)thread_kernel<CosmologyProblem, true> : (void *)thread_kernel<CosmologyProblem>);
     sp.smem = 0;
     // A batch of at most 256 cells per SM runs as one wave spread over every
     // SM, at most 8 warps of about 2 cells each per SM: 1024 Robertson cells
@@ -1327,6 +1330,17 @@ int sunb_set_linear_solver(sunb_ctx *ctx, int solver)
     // the other kernel variant: its shared-memory attribute and occupancy
     // (the same mapping), then the scratch for its resident groups
     return configure_mech(ctx, ctx->L, ctx->cells_per_cta);
+}
+
+int sunb_set_method(sunb_ctx *ctx, int method)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (method != SUNB_METHOD_BDF && method != SUNB_METHOD_ERK)
+        return fail(ctx, SUNB_ILL_INPUT, "method must be SUNB_METHOD_BDF or SUNB_METHOD_ERK");
+    if (method == SUNB_METHOD_ERK && ctx->kind != SUNB_ROBERTSON && ctx->kind != SUNB_COSMOLOGY)
+        return fail(ctx, SUNB_ILL_INPUT, "the explicit method is built for thread-per-cell kinds only");
+    ctx->method = method;
+    return SUNB_SUCCESS;
 }
 
 int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol, double eta,
