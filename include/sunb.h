@@ -167,8 +167,11 @@ int sunb_set_jacobian(sunb_ctx *ctx, int mode);
  * configuration has more resident groups, and frees it in sunb_destroy.  Takes effect at the next sunb_integrate or
  * sunb_graph_capture.  SUNB_ILL_INPUT for other values, for kinds without
  * mechanism cells, and with adjoint tapes (the adjoint differentiates the
- * direct solver's iteration); SUNB_CUDA_ERROR if the scratch cannot be
- * allocated. */
+ * direct solver's iteration); SUNB_MEM_FAIL if the scratch cannot be
+ * allocated (the previous solver then stays selected).  A later
+ * configuration change (the autotuner's) that cannot grow the scratch makes
+ * sunb_integrate and sunb_graph_capture fail with SUNB_MEM_FAIL before any
+ * launch. */
 #define SUNB_LS_DIRECT 0
 #define SUNB_LS_GMRES 1
 int sunb_set_linear_solver(sunb_ctx *ctx, int solver);

@@ -819,9 +819,23 @@ static int ensure_krylov(sunb_ctx *ctx)
     if (ctx->d_krylov) cudaFree(ctx->d_krylov);
     ctx->d_krylov = nullptr;
     ctx->krylov_cap = 0;
-    CU(cudaMalloc(&ctx->d_krylov, 8 * need));
+    if (cudaMalloc(&ctx->d_krylov, 8 * need) != cudaSuccess) {
+        cudaGetLastError();
+        ctx->d_krylov = nullptr;
+        return fail(ctx, SUNB_MEM_FAIL, "GMRES scratch: device allocation failed");
+    }
     ctx->krylov_cap = need;
     return SUNB_SUCCESS;
+}
+
+// Whether a mechanism launch of the current configuration may run: the
+// Krylov kernel needs scratch for every lane group of its grid.
+static int krylov_ready(sunb_ctx *ctx)
+{
+    if (ctx->lin_solver != 1) return SUNB_SUCCESS;
+    const size_t need = (size_t)ctx->num_sms * ctx->ctas_per_sm * ctx->cells_per_cta * krylov_doubles(ctx->off.N);
+    if (ctx->d_krylov && ctx->krylov_cap >= need) return SUNB_SUCCESS;
+    return fail(ctx, SUNB_MEM_FAIL, "GMRES scratch missing for this configuration");
 }
 
 // Cells per CTA for lanes-per-cell L: the count that keeps the most cells
@@ -912,6 +926,8 @@ static int launch_mech(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
                        long long n_mech_override = -1)
 {
     const bool cosmo = ctx->kind == SUNB_MIXED;
+    const int kr = krylov_ready(ctx);
+    if (kr != SUNB_SUCCESS) return kr;
     MechArgs a = mech_args(ctx, y, t0, tout, status);
     if (n_mech_override >= 0) {   // autotuning trial: mechanism cells only, from a scratch copy
         a.n_mech = n_mech_override;
@@ -1119,6 +1135,8 @@ static int step_config(sunb_ctx *ctx, double *y, double t0, double tout, int32_t
     const bool cosmo = ctx->kind == SUNB_MIXED;
     LaunchSpec &m = sp[0];
     m.thread = false;
+    const int kr = krylov_ready(ctx);
+    if (kr != SUNB_SUCCESS) return kr;
     m.ma = mech_args(ctx, y, t0, tout, status);
     m.func = pick_mech_kernel(ctx->L, ctx->precision, cosmo, ctx->lin_solver == 1);
     m.smem = mech_smem(ctx, ctx->cells_per_cta, ctx->L).bytes;
@@ -1326,10 +1344,19 @@ int sunb_set_linear_solver(sunb_ctx *ctx, int solver)
     if (solver == SUNB_LS_GMRES && ctx->d_tape)
         return fail(ctx, SUNB_ILL_INPUT, "the adjoint needs the direct solver");
     if (ctx->kind != SUNB_MECHANISM && ctx->kind != SUNB_MIXED) return SUNB_SUCCESS;   // LU, as always
+    const int before = ctx->lin_solver;
     ctx->lin_solver = solver;
     // the other kernel variant: its shared-memory attribute and occupancy
-    // (the same mapping), then the scratch for its resident groups
-    return configure_mech(ctx, ctx->L, ctx->cells_per_cta);
+    // (the same mapping), then the scratch for its resident groups; on
+    // failure the previous solver stays selected
+    const int rc = configure_mech(ctx, ctx->L, ctx->cells_per_cta);
+    if (rc != SUNB_SUCCESS) {
+        const std::string why = ctx->err;
+        ctx->lin_solver = before;
+        configure_mech(ctx, ctx->L, ctx->cells_per_cta);
+        ctx->err = why;
+    }
+    return rc;
 }
 
 int sunb_set_method(sunb_ctx *ctx, int method)
