@@ -362,7 +362,11 @@ def cpu_baseline(w, budget_s=12.0):
     """The oracle as it stands, on the host's cores, on a bounded sample of
     the workload (the first n cells; n grown until the sample takes a
     fraction of budget_s), extrapolated to the full batch.  For the adjoint
-    workload the oracle runs its forward, replay and adjoint."""
+    workload the oracle runs its forward, replay and adjoint.  The variant
+    flags select the oracle's counterpart where the GPU run uses one:
+    difference-quotient Jacobians and GMRES for mechanism cells, the
+    explicit method for thread-per-cell kinds, typical-value tolerances from
+    the whole batch's initial state."""
     import oracle
     nth = oracle.num_threads()
     if w["kind"] == "mixed":
@@ -382,8 +386,17 @@ def cpu_baseline(w, budget_s=12.0):
                 oracle.adjoint_sqerr(pb, sample["y0"][:n], sample["target"][:n], sample["t0"],
                                      sample["tout"], 1e-6, 1e-10, cap=4096, nthreads=nth)
             else:
-                oracle.integrate(pb, sample["y0"][:n], sample["t0"], sample["tout"], 1e-6, 1e-10,
-                                 nthreads=nth)
+                kind = "cosmology" if ww == "cosmology" else ww["kind"]
+                opts = {}
+                if kind == "mechanism":
+                    opts = dict(jac_mode=1 if JACOBIAN_DQ else 0, lin_solver=1 if LINEAR_GMRES else 0)
+                elif METHOD_ERK:
+                    opts = dict(method=1)
+                atol = 1e-10
+                if TYPICAL_ETA is not None and w["kind"] != "mixed":
+                    atol = oracle.typical_atol(w["y0"], TYPICAL_ETA)
+                oracle.integrate(pb, sample["y0"][:n], sample["t0"], sample["tout"], 1e-6, atol,
+                                 nthreads=nth, **opts)
             dt = time.perf_counter() - t
             if dt > budget_s / len(parts) / 4 or n >= Cfull:
                 break
@@ -392,6 +405,15 @@ def cpu_baseline(w, budget_s=12.0):
         descr.append(f"first {n} of {Cfull} cells ({dt:.1f} s)")
     return dict(value=sum(p[1] for p in parts) / total_s, unit=UNIT, cores=nth, kind="oracle",
                 sample="; ".join(descr) + ", extrapolated to the full batch")
+
+
+def variant_config():
+    """The config keys that name the method variant a run uses."""
+    return {"rtol": 1e-6,
+            "atol": 1e-10 if TYPICAL_ETA is None else f"typical values, eta {TYPICAL_ETA:g}",
+            "jacobian": "difference quotients" if JACOBIAN_DQ else "analytic",
+            "linear_solver": "GMRES (matrix-free)" if LINEAR_GMRES else "direct (LU)",
+            "method": "explicit RK 4(3)" if METHOD_ERK else "BDF"}
 
 
 # --------------------------------------------------------------------- main
@@ -454,7 +476,7 @@ def main():
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
                 "ms_per_step": 1e3 * C / cb["value"], "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name, "rtol": 1e-6, "atol": 1e-10},
+                "config": {"workload": workload_name, **variant_config()},
                 "cpu_baseline": cb,
                 "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
@@ -511,11 +533,7 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name, "rtol": 1e-6,
-                       "atol": 1e-10 if TYPICAL_ETA is None else f"typical values, eta {TYPICAL_ETA:g}",
-                       "jacobian": "difference quotients" if JACOBIAN_DQ else "analytic",
-                       "linear_solver": "GMRES (matrix-free)" if LINEAR_GMRES else "direct (LU)",
-                       "method": "explicit RK 4(3)" if METHOD_ERK else "BDF",
+            "config": {"workload": workload_name, **variant_config(),
                        "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
                        "mapping": res["mapping"][:3] if res["mapping"] else None,
                        "l2": "flushed between steps (512 MiB write)"},

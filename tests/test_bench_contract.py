@@ -26,3 +26,17 @@ def test_reference_arm_prints_one_contract_line():
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
     assert d["config"]["workload"].startswith("robertson")
+
+
+def test_variant_flags_reach_the_reference_arm_and_are_validated():
+    """The reference arm times the oracle's counterpart of a variant (here
+    the explicit method) and names it in its config; a variant the GPU path
+    does not offer for a workload is refused before any work."""
+    out = subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--workload", "robertson",
+                          "--method", "erk", "--cells", "8", "--steps", "1", "--warmup", "3"], cwd=ROOT,
+                         capture_output=True, text=True, timeout=600, check=True).stdout
+    d = json.loads([l for l in out.splitlines() if l.strip().startswith("{")][0])
+    assert d["config"]["method"] == "explicit RK 4(3)" and d["config"]["linear_solver"] == "direct (LU)"
+    r = subprocess.run([sys.executable, "bench.py", "--workload", "mech22", "--method", "erk"], cwd=ROOT,
+                       capture_output=True, text=True, timeout=300)
+    assert r.returncode == 2 and "thread-per-cell" in r.stderr
