@@ -11,7 +11,11 @@
  * Eq. wrms, the modified Newton iteration and stopping test of
  * Eq. stop_newton, a dense Jacobian and a pivoted LU (Table 1, approach 2A;
  * Sec. 4.1.4, 4.1.6).  Unlike the paper's batches, cells do not advance in
- * lock-step: every cell chooses its own steps and orders.
+ * lock-step: every cell chooses its own steps and orders.  The variants
+ * the paper compares are options of a context: typical-value absolute
+ * tolerances (Sec. 4.1.3), difference-quotient Jacobians (approaches
+ * 3A/3B), matrix-free GMRES linear solves (approaches 1A/1B) and an
+ * explicit Runge-Kutta method (Sec. 4.1.5).
  *
  * Conventions
  *  - State arrays are cell-contiguous ("CY" order, Sec. 4.1.2): y[c*N + i].

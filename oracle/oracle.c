@@ -46,6 +46,12 @@
  *  - first step from the starting-step algorithm of Hairer, Norsett and
  *    Wanner (Solving ODEs I, Sec. II.4) with the WRMS norm;
  *  - every call is a cold start at order 1 and lands exactly on tout.
+ *
+ * Options select the variants the paper compares: a forward-difference
+ * Jacobian (approaches 3A/3B), GMRES linear solves of an inexact Newton
+ * iteration (approaches 1A/1B; gmres_solve), and, instead of the BDF, an
+ * explicit adaptive Runge-Kutta method (Sec. 4.1.5; erk_cell).  Each
+ * carries its readings beside its code.
  */
 #include <complex.h>
 #include <float.h>
