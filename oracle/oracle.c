@@ -214,12 +214,27 @@ EXPORT void orc_bdf_l(int q, const double *xi, double *l)
         for (int j = i + 1; j >= 1; --j) l[j] += l[j - 1] / xi[i];
 }
 
-/* C_q = 1 / (1 + l_1 xi_{q+1}): the estimate E = C_q Delta. */
+/* C_q = 1 / (1 + l_1 xi_{q+1}): the estimate E = C_q Delta.  The
+ * integrator and the fixed-step routine call this same function. */
+static double error_constant(double l1, double xi_qp1)
+{
+    return 1.0 / (1.0 + l1 * xi_qp1);
+}
+
 EXPORT double orc_error_constant(int q, const double *xi)
 {
     double l[QMAX + 2];
     orc_bdf_l(q, xi, l);
-    return 1.0 / (1.0 + l[1] * xi[q]);
+    return error_constant(l[1], xi[q]);
+}
+
+/* Nordsieck prediction z <- z Pascal(q): the repeated in-place sums
+ * z_{j-1} += z_j (the integrator and the fixed-step routine). */
+static void predict(int q, int n, double *z)
+{
+    for (int k = 0; k < q; ++k)
+        for (int j = q; j > k; --j)
+            for (int i = 0; i < n; ++i) z[(j - 1) * n + i] += z[j * n + i];
 }
 
 /* Lower the order of the Nordsieck array z (columns 0..q, n values each) by
@@ -519,13 +534,11 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
         double dsm = 0.0, Cq = 0.0, l[QMAX + 2], xi[QMAX + 2];
         for (;;) {  /* attempts */
             memcpy(zsave, z, sizeof(double) * (q + 1) * n);
-            for (int k = 0; k < q; ++k)               /* predict */
-                for (int j = q; j > k; --j)
-                    for (int i = 0; i < n; ++i) z[(j - 1) * n + i] += z[j * n + i];
+            predict(q, n, z);
             bdf_xi(q + 1, h, hist, xi);
             orc_bdf_l(q, xi, l);
             const double l1 = l[1], gamma = h / l1;
-            Cq = 1.0 / (1.0 + l1 * xi[q]);
+            Cq = error_constant(l1, xi[q]);
             int fresh = 0, conv = 0;
             const int krylov = op->lin_solver == 1;
             if (krylov) { have_M = 1; fresh = 1; gamma_M = gamma; }   /* no matrix to keep */
@@ -874,9 +887,7 @@ EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int 
     memcpy(hist, hist_init, sizeof(double) * (QMAX + 1));
     for (int i = 0; i < n; ++i) w[i] = 1.0;
     for (int step = 0; step < nsteps; ++step) {
-        for (int k = 0; k < q; ++k)
-            for (int j = q; j > k; --j)
-                for (int i = 0; i < n; ++i) z[(j - 1) * n + i] += z[j * n + i];
+        predict(q, n, z);
         bdf_xi(q + 1, h, hist, xi);
         orc_bdf_l(q, xi, l);
         double gamma = h / l[1];
@@ -896,7 +907,7 @@ EXPORT int orc_bdf_fixed(const orc_problem *pb, long cell, int q, double h, int 
             }
             if (dmax <= 1e-15 * ymax || dmax == 0.0) break;
         }
-        double Cq = 1.0 / (1.0 + l[1] * xi[q]);
+        double Cq = error_constant(l[1], xi[q]);
         for (int j = 0; j <= q; ++j)
             for (int i = 0; i < n; ++i) z[j * n + i] += l[j] * acor[i];
         for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];

@@ -157,6 +157,9 @@ def special_mechanism(kind):
     ``"dimer"``: 2A <=> A2 with thermodynamics chosen so that the reaction
     enthalpy vanishes (temperature constant) while the mole number changes,
     which exercises the pressure factor of the equilibrium constant.
+    ``"dissociation"``: the same species and thermodynamics with the
+    reaction written A2 <=> 2A, so that the mole number grows (the other
+    sign of the pressure factor); its equilibrium is the dimer's.
     """
     if kind == "isomer":
         comp = np.array([[1, 1, 0], [1, 1, 0]])
@@ -167,7 +170,7 @@ def special_mechanism(kind):
         lnA = np.array([np.log(2.0e5)])
         beta = np.array([0.5])
         Ea = np.array([12000.0])
-    elif kind == "dimer":
+    elif kind in ("dimer", "dissociation"):
         comp = np.array([[1, 0, 1], [2, 0, 2]])
         # h/RT of A2 equals twice that of A: a_i(A2) = 2 a_i(A) for i = 1..6.
         a = np.array([3.0, 1e-4, 0, 0, 0, -400.0, 1.5])
@@ -179,6 +182,9 @@ def special_mechanism(kind):
         lnA = np.array([np.log(3.0e12)])
         beta = np.array([0.0])
         Ea = np.array([5000.0])
+        if kind == "dissociation":
+            react, prod = prod, react
+            lnA = np.array([np.log(1.0e6)])
     else:
         raise ValueError(kind)
     W = comp.astype(np.float64) @ ELEMENT_MASS
