@@ -157,6 +157,10 @@ def special_mechanism(kind):
     ``"dimer"``: 2A <=> A2 with thermodynamics chosen so that the reaction
     enthalpy vanishes (temperature constant) while the mole number changes,
     which exercises the pressure factor of the equilibrium constant.
+    ``"isomer_thermo"``: A <=> B of equal composition with different,
+    fully temperature-dependent NASA polynomials, so the reaction releases
+    heat and its equilibrium constant depends on every entropy and
+    enthalpy coefficient.
     ``"dissociation"``: the same species and thermodynamics with the
     reaction written A2 <=> 2A, so that the mole number grows (the other
     sign of the pressure factor); its equilibrium is the dimer's.
@@ -170,6 +174,15 @@ def special_mechanism(kind):
         lnA = np.array([np.log(2.0e5)])
         beta = np.array([0.5])
         Ea = np.array([12000.0])
+    elif kind == "isomer_thermo":
+        comp = np.array([[1, 1, 0], [1, 1, 0]])
+        nasa = np.array([[3.5, 2e-4, -1e-7, 3e-11, -2e-15, 100.0, 2.0],
+                         [3.2, 5e-4, -2e-7, 4e-11, -3e-15, -500.0, 3.1]])
+        react = np.array([[0, -1, -1]], dtype=np.int32)
+        prod = np.array([[1, -1, -1]], dtype=np.int32)
+        lnA = np.array([np.log(1.0e7)])
+        beta = np.array([0.0])
+        Ea = np.array([20000.0])
     elif kind in ("dimer", "dissociation"):
         comp = np.array([[1, 0, 1], [2, 0, 2]])
         # h/RT of A2 equals twice that of A: a_i(A2) = 2 a_i(A) for i = 1..6.

@@ -183,6 +183,38 @@ def test_isomerisation_relaxes_exponentially():
         assert abs(y[0, 2] - T) < 1e-9 * T
 
 
+def _g_over_RT_by_quadrature(a, T):
+    """g/RT = h/RT - s/R of one species from its cp/R polynomial alone:
+    h/RT = (a6 + int_0^T cp/R dT') / T and
+    s/R = a7 + a1 ln T + int_0^T (cp/R - a1) / T' dT' (a regular integrand),
+    both by Gauss-Legendre quadrature, independently of the closed forms."""
+    x, wq = np.polynomial.legendre.leggauss(8)
+    Tq = 0.5 * T * (x + 1.0)
+    cpR = sum(a[i] * Tq ** i for i in range(5))
+    hRT = (a[5] + 0.5 * T * np.sum(wq * cpR)) / T
+    sR = a[6] + a[0] * np.log(T) + 0.5 * T * np.sum(wq * (cpR - a[0]) / Tq)
+    return hRT - sR
+
+
+def test_adiabatic_isomerisation_reaches_the_equilibrium_of_its_final_temperature():
+    """A <=> B (equal composition) with different temperature-dependent
+    thermodynamics releases heat; at equilibrium Y_B / Y_A = Kc(T_final) =
+    exp(-(g_B - g_A)/RT_final), with g/RT from quadrature of cp/R (every
+    enthalpy and entropy coefficient matters), and the mixture enthalpy is
+    conserved on the way."""
+    mech = synth.special_mechanism("isomer_thermo")
+    pb, y0 = _one_cell(mech, [0.9, 0.1, 1400.0])
+    y, _, _, worst = oracle.integrate(pb, y0, 0.0, 1.0, 1e-11, 1e-15)
+    assert worst == 0
+    Ya, Yb, Tf = y[0]
+    assert abs(Tf - 1400.0) > 1.0                       # the reaction changed T
+    dg = _g_over_RT_by_quadrature(mech.nasa[1], Tf) - _g_over_RT_by_quadrature(mech.nasa[0], Tf)
+    assert abs(Yb / Ya - np.exp(-dg)) < 1e-8 * np.exp(-dg)
+    H0, s0 = _enthalpy_by_quadrature(mech, y0[:2], y0[2])
+    H1, _ = _enthalpy_by_quadrature(mech, y[0, :2], Tf)
+    assert abs(H1 - H0) < 1e-9 * s0
+
+
 @pytest.mark.parametrize("direction", ["dimer", "dissociation"])
 def test_dimerisation_reaches_pressure_dependent_equilibrium(direction):
     """2A <=> A2 with zero reaction enthalpy (T constant): at equilibrium

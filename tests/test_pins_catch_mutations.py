@@ -2,11 +2,13 @@
 case plants one mistake (a dropped term, a wrong sign or index, a
 transposed operand, a mistyped coefficient) in a copy of the oracle's C
 source, builds it, and runs the oracle's pin tests against it, which must
-fail.  The mistakes are planted in copies on the CPU only."""
+fail.  The mistakes are planted in copies on the CPU only; the cases run
+concurrently, one core each."""
 import os
 import shutil
 import subprocess
 import sys
+from concurrent.futures import ThreadPoolExecutor
 
 import pytest
 
@@ -44,6 +46,29 @@ MUTATIONS = [
      "for (int i = 0; i < dnu; ++i) Kc *= patm_RT;", "for (int i = 0; i < dnu; ++i) Kc /= patm_RT;"),
     ("temperature equation with the wrong sign", "rhs_impl.h",
      "f[K] = -(ORC_RU * T * hw) / (rho * cp);", "f[K] = (ORC_RU * T * hw) / (rho * cp);"),
+    ("Arrhenius activation term with the wrong sign", "rhs_impl.h",
+     "- pb->Ea[j] / (ORC_RC * T));", "+ pb->Ea[j] / (ORC_RC * T));"),
+    ("NASA enthalpy's T^4 coefficient mistyped", "rhs_impl.h",
+     "+ a[4] * T4 / 5.0 + a[5] / T;", "+ a[4] * T4 / 4.0 + a[5] / T;"),
+    ("NASA entropy's T^2 coefficient mistyped", "rhs_impl.h",
+     "+ a[2] * T2 / 2.0 + a[3] * T3 / 3.0", "+ a[2] * T2 / 3.0 + a[3] * T3 / 3.0"),
+    ("cooling segment evaluated from the wrong knot", "rhs_impl.h",
+     "REAL lam = EXPF(v[lo] + slope * (lnT - x[lo]));", "REAL lam = EXPF(v[lo] + slope * (lnT - x[lo + 1]));"),
+    ("heating law about the wrong temperature", "rhs_impl.h",
+     "EXPF(-0.7 * (lnT - ORC_LN1E4))", "EXPF(-0.7 * (lnT + ORC_LN1E4))"),
+    ("step-ratio history shifted by one", "oracle.c",
+     "for (int i = 1; i < m; ++i) { s += hist[i - 1]; xi[i] = s / h; }",
+     "for (int i = 1; i < m; ++i) { s += hist[i]; xi[i] = s / h; }"),
+    ("LU forward substitution on the transposed factor", "oracle.c",
+     "for (int j = 0; j < i; ++j) b[i] -= LU[i * n + j] * b[j];",
+     "for (int j = 0; j < i; ++j) b[i] -= LU[j * n + i] * b[j];"),
+    ("Gram-Schmidt against the wrong basis vector", "oracle.c",
+     "for (int i = 0; i < n; ++i) h += vn[i] * V[m * n + i];",
+     "for (int i = 0; i < n; ++i) h += vn[i] * V[j * n + i];"),
+    ("Givens rotation with the wrong sign", "oracle.c",
+     "H[(m + 1) * maxl + j] = -sn[m] * a + cs[m] * bb;", "H[(m + 1) * maxl + j] = sn[m] * a + cs[m] * bb;"),
+    ("complex-step Jacobian scaled twice", "oracle.c",
+     "J[i * n + j] = cimag(fc[i]) / s;", "J[i * n + j] = cimag(fc[i]) / (2.0 * s);"),
 ]
 
 
@@ -52,17 +77,39 @@ def _pin_tests():
                   if f.startswith("test_oracle_") and f.endswith(".py"))
 
 
-@pytest.mark.parametrize("what,fname,old,new", MUTATIONS, ids=[m[0] for m in MUTATIONS])
-def test_planted_mistake_fails_a_pin(tmp_path, what, fname, old, new):
+def _run_mutant(workdir, fname, old, new):
+    """Build the oracle with one mistake planted and run the pins on it:
+    (pins' exit code, the tail of their output)."""
+    os.makedirs(workdir)
     for f in ("oracle.c", "oracle.h", "rhs_impl.h"):
-        shutil.copy(os.path.join(ORACLE, f), tmp_path / f)
-    src = (tmp_path / fname).read_text()
-    assert src.count(old) == 1, f"mutation site not unique or missing: {old}"
-    (tmp_path / fname).write_text(src.replace(old, new))
-    so = str(tmp_path / "liboracle_mut.so")
+        shutil.copy(os.path.join(ORACLE, f), os.path.join(workdir, f))
+    with open(os.path.join(workdir, fname)) as fh:
+        src = fh.read()
+    if src.count(old) != 1:
+        return None, f"mutation site not unique or missing: {old}"
+    with open(os.path.join(workdir, fname), "w") as fh:
+        fh.write(src.replace(old, new))
+    so = os.path.join(workdir, "liboracle_mut.so")
     subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=gnu11",
-                           str(tmp_path / "oracle.c"), "-o", so, "-lm"])
-    env = dict(os.environ, SUNB_ORACLE_LIB=so)
+                           os.path.join(workdir, "oracle.c"), "-o", so, "-lm"])
+    env = dict(os.environ, SUNB_ORACLE_LIB=so, OMP_NUM_THREADS="1")
     r = subprocess.run([sys.executable, "-m", "pytest", "-x", "-q", "-p", "no:cacheprovider", *_pin_tests()],
                        cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
-    assert r.returncode == 1, f"no pin caught: {what}\n{r.stdout[-2000:]}"
+    return r.returncode, r.stdout[-2000:]
+
+
+@pytest.fixture(scope="module")
+def outcomes(tmp_path_factory):
+    """Every mutant, built and pinned concurrently (one core each)."""
+    base = tmp_path_factory.mktemp("mutants")
+    workers = max(1, min(len(MUTATIONS), os.cpu_count() or 1))
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        futures = {m[0]: ex.submit(_run_mutant, str(base / f"m{i}"), *m[1:]) for i, m in enumerate(MUTATIONS)}
+        return {k: f.result() for k, f in futures.items()}
+
+
+@pytest.mark.parametrize("what", [m[0] for m in MUTATIONS])
+def test_planted_mistake_fails_a_pin(outcomes, what):
+    code, out = outcomes[what]
+    assert code is not None, out
+    assert code == 1, f"no pin caught: {what}\n{out}"
