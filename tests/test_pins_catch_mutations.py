@@ -69,6 +69,16 @@ MUTATIONS = [
      "H[(m + 1) * maxl + j] = -sn[m] * a + cs[m] * bb;", "H[(m + 1) * maxl + j] = sn[m] * a + cs[m] * bb;"),
     ("complex-step Jacobian scaled twice", "oracle.c",
      "J[i * n + j] = cimag(fc[i]) / s;", "J[i * n + j] = cimag(fc[i]) / (2.0 * s);"),
+    ("stale-matrix scaling with the ratio inverted", "oracle.c",
+     "double c = 2.0 / (1.0 + gamma / gamma_M);", "double c = 2.0 / (1.0 + gamma_M / gamma);"),
+    ("Newton tolerance ten times too loose", "oracle.c",
+     "if (R * dn * Cq < 0.1) { conv = 1; break; }", "if (R * dn * Cq < 1.0) { conv = 1; break; }"),
+    ("error test on the correction without C_q", "oracle.c",
+     "dsm = Cq * wrms(n, acor, w);", "dsm = wrms(n, acor, w);"),
+    ("explicit method without its cap after repeated rejections", "oracle.c",
+     "if (nef >= 2) eta = fmin(eta, 0.3);", ""),
+    ("typical value ignoring NaN cells", "oracle.c",
+     "if (nan || C < 1 ||", "if (C < 1 ||"),
 ]
 
 
