@@ -86,6 +86,8 @@ def lib():
         L.orc_tape_free.argtypes = [ctypes.c_void_p]
         L.orc_tape_count.argtypes = [ctypes.c_void_p]
         L.orc_tape_count.restype = ctypes.c_int
+        L.orc_tape_map.argtypes = [ctypes.c_void_p, ctypes.c_int, _dp]
+        L.orc_tape_map.restype = ctypes.c_int
         L.orc_forward_tape.argtypes = [PP, ctypes.c_long, _dp, ctypes.c_double, ctypes.c_double,
                                        ctypes.POINTER(Options), _ip, ctypes.c_void_p]
         L.orc_forward_tape.restype = ctypes.c_int
@@ -309,6 +311,13 @@ class Tape:
     @property
     def steps(self):
         return lib().orc_tape_count(self.ptr)
+
+    def column_map(self, r):
+        """Step r's Nordsieck column map [6, 6] (row = output column)."""
+        P = np.empty((6, 6))
+        if lib().orc_tape_map(self.ptr, r, _d(P)):
+            raise IndexError(r)
+        return P
 
     def __del__(self):
         if getattr(self, "ptr", None):

@@ -955,6 +955,14 @@ EXPORT void orc_tape_free(orc_tape *tp)
 
 EXPORT int orc_tape_count(const orc_tape *tp) { return tp->overflow ? -1 : tp->count; }
 
+/* Record r's column map [6][6] (row = output column), for tests. */
+EXPORT int orc_tape_map(const orc_tape *tp, int r, double *P)
+{
+    if (r < 0 || r >= tp->count) return -1;
+    memcpy(P, tp->rec + (size_t)r * TAPE_R(tp->n) + tp->n, sizeof(double) * 36);
+    return 0;
+}
+
 EXPORT int orc_forward_tape(const orc_problem *pb, long cell, double *y, double t0, double tout,
                             const orc_options *op, orc_stats *st, orc_tape *tp)
 {

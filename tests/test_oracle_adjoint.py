@@ -62,6 +62,41 @@ def test_adjoint_matches_central_differences_of_the_frozen_map(case):
             assert abs(g[j, w] - fd) <= 1e-4 * scale[w] + noise, (j, w, g[j, w], fd)
 
 
+def test_adjoint_matches_central_differences_on_sensitive_cells():
+    """mech22 cells of the adjoint workload (dt 1e-5, about 900 accepted
+    steps with several order decreases each): on the reactions the loss is
+    most sensitive to, the gradient with respect to ln A and Ea matches
+    central differences of the frozen map to 1e-5 relative, where the
+    differences' rounding noise is below 1e-4 of the gradient (a
+    non-vacuous check, unlike rounding-level sensitivities)."""
+    w = synth.workloads.adjoint(2)
+    mech = w["mech"]
+    K = mech.n_species
+    for c in range(2):
+        pb = oracle.OracleProblem(oracle.MECHANISM, mech.n_vars, w["params"][c:c + 1], mech=mech)
+        _, st, tp = oracle.forward_tape(pb, w["y0"][c], w["t0"], w["tout"], 1e-6, 1e-10)
+        assert st[7] == 0
+        decreases = sum(np.any(np.abs(P - np.diag(np.diag(P))) > 0)
+                        for P in (tp.column_map(r) for r in range(tp.steps)))
+        assert decreases >= 1
+        target = w["target"][c]
+        y, g = _loss_grad(pb, tp, K, target)
+        L0 = np.sum((y[:K] - target) ** 2)
+        lnA0, Ea0 = pb.lnA.copy(), pb.Ea.copy()
+        for j in np.argsort(-np.abs(g[:, 0]))[:3]:
+            for wi, base in ((0, lnA0), (1, Ea0)):
+                d = 1e-6 * max(1.0, abs(base[j]))
+                vals = []
+                for sgn in (1.0, -1.0):
+                    pb.lnA[:], pb.Ea[:] = lnA0, Ea0
+                    (pb.lnA if wi == 0 else pb.Ea)[j] += sgn * d
+                    vals.append(np.sum((oracle.replay_tape(pb, tp)[:K] - target) ** 2))
+                pb.lnA[:], pb.Ea[:] = lnA0, Ea0
+                fd = (vals[0] - vals[1]) / (2 * d)
+                assert 2e-14 * L0 / d < 1e-4 * abs(g[j, wi])
+                assert abs(g[j, wi] - fd) <= 1e-5 * abs(g[j, wi]), (c, j, wi, g[j, wi], fd)
+
+
 def test_adjoint_isomerisation_closed_form():
     """A <=> B: Y_A(t) = Y_eq + (Y_A0 - Y_eq) exp(-s t), s = kf (1 + 1/Kc),
     so dY_A/d ln A = -(Y_A0 - Y_eq) s t exp(-s t) and d/dEa = -d/d ln A / (Rc T)."""

@@ -79,6 +79,15 @@ MUTATIONS = [
      "if (nef >= 2) eta = fmin(eta, 0.3);", ""),
     ("typical value ignoring NaN cells", "oracle.c",
      "if (nan || C < 1 ||", "if (C < 1 ||"),
+    ("adjoint solve with the untransposed Newton matrix", "oracle.c",
+     "Mt[a * n + b] = (a == b ? 1.0 : 0.0) - gamma * J[b * n + a];",
+     "Mt[a * n + b] = (a == b ? 1.0 : 0.0) - gamma * J[a * n + b];"),
+    ("adjoint of a_n with the wrong sign of the z_1 term", "oracle.c",
+     "lam[n + i] -= il1 * ld[i];", "lam[n + i] += il1 * ld[i];"),
+    ("activation-energy gradient with the wrong sign", "oracle.c",
+     "grad[2 * j + 1] += -scale * d / (ORC_RC * T);", "grad[2 * j + 1] += scale * d / (ORC_RC * T);"),
+    ("order decrease subtracting the wrong multiple", "oracle.c",
+     "z[j * n + k] -= e[j - 1] * z[q * n + k];", "z[j * n + k] -= e[j] * z[q * n + k];"),
 ]
 
 
