@@ -55,3 +55,24 @@ def test_version_and_null_arguments_without_gpu(lib):
 def test_library_is_built_for_sm_103a():
     from paper_2405_01713_b300 import build
     assert "arch=compute_103a,code=sm_103a" in build.FLAGS
+
+
+def test_binding_constants_equal_the_header():
+    """Every SUNB_* value the header defines (enumerators and #defines)
+    has the same value in the binding, under its name without the prefix
+    (status codes also in the binding's STATUS table)."""
+    import paper_2405_01713_b300 as sb
+    txt = open(os.path.join(ROOT, "include", "sunb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    vals = {k: int(v) for k, v in re.findall(r"\bSUNB_([A-Z0-9_]+)\s*=\s*(-?\d+)", txt)}
+    vals.update({k: int(v) for k, v in re.findall(r"#define\s+SUNB_([A-Z0-9_]+)\s+(-?\d+)", txt)})
+    assert len(vals) >= 20
+    statuses = {k for k in vals if vals[k] <= 0 and k in sb.STATUS.values()}
+    for name, v in vals.items():
+        if name in statuses:
+            assert sb.STATUS[v] == name
+        if hasattr(sb, name):
+            assert getattr(sb, name) == v, name
+    for name in ("ROBERTSON", "MECHANISM", "COSMOLOGY", "MIXED", "FP64", "MIXED32",
+                 "SCHED_QUEUE", "SCHED_STATIC", "LS_DIRECT", "LS_GMRES", "METHOD_BDF", "METHOD_ERK"):
+        assert getattr(sb, name) == vals[name], name
