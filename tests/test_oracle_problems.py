@@ -308,6 +308,24 @@ def test_heating_power_law_closed_form():
     assert abs(y[0, 0] - ex) < 1e-9 * ex
 
 
+def test_heating_and_cooling_reach_their_balance():
+    """Lambda = c T^alpha and H = G (T/1e4)^-0.7 with F = 0 balance at
+    T* = (G 1e4^0.7 / c)^(1/(alpha + 0.7)); the gas relaxes to it from
+    above and from below (rate rho (alpha + 0.7) Lambda(T*)/T*)."""
+    alpha, lam4, rho = 0.6, 5e3, 2.0
+    c = lam4 / 1e4 ** alpha
+    Tstar = 2.0e4
+    G = c * Tstar ** alpha * (Tstar / 1e4) ** 0.7
+    tab = _straight_table(alpha, lam4, G)
+    pb = oracle.OracleProblem(oracle.COSMOLOGY, 1, np.array([[rho, 0.0]] * 2), table=tab)
+    closed = (G * 1e4 ** 0.7 / c) ** (1 / (alpha + 0.7))
+    assert abs(closed - Tstar) < 1e-9 * Tstar
+    rate = rho * (alpha + 0.7) * c * Tstar ** alpha / Tstar
+    y, _, _, worst = oracle.integrate(pb, np.array([[5e4], [1e3]]), 0.0, 60.0 / rate, 1e-12, 1e-14)
+    assert worst == 0
+    assert np.max(np.abs(y[:, 0] - Tstar)) < 1e-9 * Tstar
+
+
 def test_constant_forcing():
     tab = _straight_table(1.0, 1e-250, 0.0)
     pb = oracle.OracleProblem(oracle.COSMOLOGY, 1, np.array([[1.0, 250.0]]), table=tab)
