@@ -9,7 +9,20 @@ raises ``ImportError`` -- there is no CPU fallback.
 Method: arXiv 2405.01713 (Balos et al.), Sec. 2 -- one variable-order,
 variable-step BDF integration per cell with WRMS error control (Eq. wrms),
 modified Newton (Eq. stop_newton), analytic dense Jacobian and pivoted LU
-(Table 1, approach 2A).
+(Table 1, approach 2A).  The variants the paper compares are options of an
+``Integrator``: ``set_typical_tolerances`` (Sec. 4.1.3), ``set_jacobian(JAC_DQ)``
+(approaches 3A/3B), ``set_linear_solver(LS_GMRES)`` (approaches 1A/1B) and
+``set_method(METHOD_ERK)`` (the explicit method of Sec. 4.1.5).
+
+Typical use, one outer step of a batch of mechanism cells::
+
+    import torch, synth, paper_2405_01713_b300 as sb
+    w = synth.workloads.mech22(4096)                 # or your own mechanism
+    it = sb.from_workload(w, precision=sb.MIXED32)   # FP32 Newton matrix
+    it.set_params(torch.tensor(w["params"], device="cuda"))
+    y = torch.tensor(w["y0"], device="cuda")         # [cells, N], in place
+    it.integrate(y, 0.0, 1e-6)
+    print(it.totals())                               # steps, f, J, ... summed
 """
 import ctypes
 import os
