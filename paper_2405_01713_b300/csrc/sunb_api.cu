@@ -1480,9 +1480,15 @@ int sunb_integrate_host(sunb_ctx *ctx, double *host_y, double t0, double tout, i
     if (!host_y) return fail(ctx, SUNB_ILL_INPUT, "y is NULL");
     const size_t ny = (size_t)ctx->C * ctx->N + (size_t)ctx->Cc;
     const size_t nc = (size_t)(ctx->C + ctx->Cc);
-    if (!ctx->d_ybuf) {
-        if (cudaMalloc(&ctx->d_ybuf, 8 * ny) != cudaSuccess || cudaMalloc(&ctx->d_sbuf, 4 * nc) != cudaSuccess)
+    if (!ctx->d_ybuf || !ctx->d_sbuf) {      // both staging buffers, or neither
+        if (cudaMalloc(&ctx->d_ybuf, 8 * ny) != cudaSuccess || cudaMalloc(&ctx->d_sbuf, 4 * nc) != cudaSuccess) {
+            cudaGetLastError();
+            cudaFree(ctx->d_ybuf);
+            cudaFree(ctx->d_sbuf);
+            ctx->d_ybuf = nullptr;
+            ctx->d_sbuf = nullptr;
             return fail(ctx, SUNB_MEM_FAIL, "cudaMalloc staging buffer");
+        }
     }
     CU(cudaMemcpyAsync(ctx->d_ybuf, host_y, 8 * ny, cudaMemcpyHostToDevice, ctx->stream));
     int rc = sunb_integrate(ctx, ctx->d_ybuf, t0, tout, host_status ? ctx->d_sbuf : nullptr);
