@@ -999,34 +999,48 @@ static int lu_batched(int32_t n, int64_t batch, MT *A, int32_t *piv, MT *b, int3
 // synchronous and leave the caller's state untouched.
 static long long resident_cells(sunb_ctx *ctx) { return (long long)ctx->num_sms * ctx->ctas_per_sm * ctx->cells_per_cta; }
 
+// Two timing events, destroyed on every return path.
+struct EventPair {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~EventPair()
+    {
+        if (a) cudaEventDestroy(a);
+        if (b) cudaEventDestroy(b);
+    }
+};
+
 static int autotune(sunb_ctx *ctx, const double *dev_y, double t0, double tout)
 {
     const bool mixed = ctx->kind == SUNB_MIXED;
     const double *ysrc = dev_y + (mixed ? ctx->Cc : 0);
-    cudaEvent_t e0, e1;
-    CU(cudaEventCreate(&e0));
-    CU(cudaEventCreate(&e1));
+    EventPair ev;
+    CU(cudaEventCreate(&ev.a));
+    CU(cudaEventCreate(&ev.b));
     double best = 1e300;
-    int bestL = ctx->L, bestc = ctx->cells_per_cta;
+    const int startL = ctx->L, startc = ctx->cells_per_cta;
+    int bestL = startL, bestc = startc;
     const int Ls[3] = {8, 16, 32};
     for (int li = 0; li < 3; ++li) {
         if (configure_mech(ctx, Ls[li]) != SUNB_SUCCESS) { ctx->tune_ms[li][0] = -1.0f; continue; }
         const long long n = std::min<long long>(ctx->tune_cells, 8 * resident_cells(ctx));
         CU(cudaMemcpyAsync(ctx->d_tune, ysrc, 8 * (size_t)n * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
-        CU(cudaEventRecord(e0, ctx->stream));
+        CU(cudaEventRecord(ev.a, ctx->stream));
         int r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, n);
-        CU(cudaEventRecord(e1, ctx->stream));
-        CU(cudaEventSynchronize(e1));
-        if (r != SUNB_SUCCESS) return r;
+        CU(cudaEventRecord(ev.b, ctx->stream));
+        CU(cudaEventSynchronize(ev.b));
+        if (r != SUNB_SUCCESS) {                 // back to the mapping it started from
+            const std::string why = ctx->err;
+            configure_mech(ctx, startL, startc);
+            ctx->err = why;
+            return r;
+        }
         float ms = 0.0f;
-        CU(cudaEventElapsedTime(&ms, e0, e1));
+        CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
         ctx->tune_ms[li][0] = ms;
         ctx->tune_ms[li][1] = (float)n;
         const double per_cell = ms / (double)n;
         if (per_cell < best) { best = per_cell; bestL = Ls[li]; bestc = ctx->cells_per_cta; }
     }
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
     ctx->tuned = true;
     return configure_mech(ctx, bestL, bestc);
 }
