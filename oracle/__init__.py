@@ -104,6 +104,20 @@ def lib():
         L.orc_gmres.restype = ctypes.c_int
         L.orc_erk_table.argtypes = [_dp, _dp, _dp]
         L.orc_erk_fixed.argtypes = [PP, ctypes.c_long, ctypes.c_double, ctypes.c_int, _dp, _dp]
+        L.orc_newton_solve.argtypes = [PP, ctypes.c_long, _dp, ctypes.c_double, ctypes.c_double,
+                                       ctypes.c_double, ctypes.c_double, ctypes.c_double, _dp, _ip, _dp,
+                                       _dp, _dp, ctypes.POINTER(ctypes.c_int)]
+        L.orc_newton_solve.restype = ctypes.c_int
+        L.orc_replay_tape_states.argtypes = [PP, ctypes.c_long, ctypes.c_void_p, _dp, _dp]
+        L.orc_replay_tape_states.restype = ctypes.c_int
+        L.orc_tape_from_decisions.argtypes = [ctypes.c_int, ctypes.c_int, _dp, ctypes.c_double, _dp,
+                                              _ip, _ip, _ip, _ip, _dp]
+        L.orc_tape_from_decisions.restype = ctypes.c_void_p
+        L.orc_follow_tape.argtypes = [PP, ctypes.c_long, ctypes.c_void_p, ctypes.c_double, _dp,
+                                      ctypes.c_int, _dp]
+        L.orc_follow_tape.restype = ctypes.c_int
+        L.orc_tape_records.argtypes = [ctypes.c_void_p, _dp, _dp]
+        L.orc_tape_records.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -324,6 +338,40 @@ class Tape:
             lib().orc_tape_free(self.ptr)
             self.ptr = None
 
+    def records(self):
+        """The tape as a dict in the layout of the CUDA library's tapes: y0, h0
+        and per accepted step y, P [6, 6], c, gamma, il1, q, qo, h, ncf, nef."""
+        n, count = self.n, max(self.steps, 0)
+        head, rec = np.empty(1 + n), np.empty((max(count, 1), n + 49))
+        lib().orc_tape_records(self.ptr, _d(head), _d(rec))
+        rec = rec[:count]
+        return dict(count=count, h0=head[0], y0=head[1:].copy(), y=rec[:, :n].copy(),
+                    P=rec[:, n:n + 36].reshape(count, 6, 6).copy(), c=rec[:, n + 36:n + 42].copy(),
+                    gamma=rec[:, n + 42].copy(), il1=rec[:, n + 43].copy(),
+                    q=rec[:, n + 44].astype(np.int32), qo=rec[:, n + 45].astype(np.int32),
+                    h=rec[:, n + 46].copy(), ncf=rec[:, n + 47].astype(np.int32),
+                    nef=rec[:, n + 48].astype(np.int32))
+
+    @classmethod
+    def from_decisions(cls, y0, h0, h, q, qo, ncf=None, nef=None, states=None):
+        """The frozen map rebuilt from a step history's control decisions
+        alone (orc_tape_from_decisions): y0, h0 and per accepted step h, q,
+        q_out (and failures); states (optional [count, n]) are stored with
+        the records for following a forward run."""
+        y0 = _f64(y0)
+        n, count = y0.shape[0], len(h)
+        i32 = lambda a: np.ascontiguousarray(np.zeros(count) if a is None else a, dtype=np.int32)
+        arrs = [_f64(h), i32(q), i32(qo), i32(ncf), i32(nef)]
+        st = None if states is None else _f64(states).reshape(count, n)
+        self = cls.__new__(cls)
+        self.n = n
+        self.ptr = lib().orc_tape_from_decisions(n, count, _d(y0), float(h0), _d(arrs[0]), _i(arrs[1]),
+                                                 _i(arrs[2]), _i(arrs[3]), _i(arrs[4]),
+                                                 _d(st) if st is not None else None)
+        if not self.ptr:
+            raise ValueError("inconsistent decisions (orders, or a non-positive step)")
+        return self
+
 
 def forward_tape(pb, y0, t0, tout, rtol, atol, cell=0, max_steps=100000, cap=8192, max_order=5):
     """Integrate one cell and record its tape: returns (y, stats, tape)."""
@@ -376,3 +424,42 @@ def adjoint_sqerr(pb, y0, target, t0, tout, rtol, atol, cap=8192, nthreads=0, ma
     nbad = lib().orc_adjoint_sqerr(pb.ref, C, _d(y0), _d(target), t0, tout, ctypes.byref(o), cap,
                                    _d(yrep), _d(grad), nthreads)
     return yrep, grad, nbad
+
+
+def replay_tape_states(pb, tape, cell=0):
+    """Final state and the exact state of every step [count, n] of the
+    tape's frozen map."""
+    y = np.empty(pb.n)
+    ys = np.empty((max(tape.steps, 1), pb.n))
+    rc = lib().orc_replay_tape_states(pb.ref, cell, tape.ptr, _d(y), _d(ys))
+    if rc:
+        raise RuntimeError(f"replay failed ({rc})")
+    return y, ys[:tape.steps]
+
+
+FOLLOW_FIELDS = ("dsm", "newton_err", "eta", "newq", "ratio_rec", "q_rec", "dsm_exact",
+                 "eta_exact", "orders_considered", "fails")
+
+
+def follow_tape(pb, tape, rtol, atol, cell=0, max_order=5):
+    """The oracle's own decisions along a forward run (orc_follow_tape):
+    a dict of per-step arrays named by FOLLOW_FIELDS."""
+    atol = np.broadcast_to(_f64(atol), (pb.n,)).copy()
+    out = np.empty((max(tape.steps, 1), 10))
+    rc = lib().orc_follow_tape(pb.ref, cell, tape.ptr, rtol, _d(atol), max_order, _d(out))
+    if rc:
+        raise RuntimeError(f"follow failed ({rc})")
+    out = out[:tape.steps]
+    return {k: out[:, i] for i, k in enumerate(FOLLOW_FIELDS)}
+
+
+def newton_solve(pb, z0, z1, h, l1, gamma, gamma_M, Cq, LU, piv, w, cell=0):
+    """One modified Newton solve of the integrator (Eq. stop_newton) with the
+    given factors of M: (converged, iterations, y, acor)."""
+    z = np.ascontiguousarray(np.stack([_f64(z0), _f64(z1)]))
+    acor, y = np.empty(pb.n), np.empty(pb.n)
+    it = ctypes.c_int()
+    conv = lib().orc_newton_solve(pb.ref, cell, _d(z), h, l1, gamma, gamma_M, Cq, _d(_f64(LU)),
+                                  _i(np.ascontiguousarray(piv, np.int32)), _d(_f64(w)), _d(acor), _d(y),
+                                  ctypes.byref(it))
+    return bool(conv), it.value, y, acor

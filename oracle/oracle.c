@@ -296,6 +296,47 @@ static double eta_from(double dsm, int p, double bias)
     return 1.0 / (pow(bias * dsm, 1.0 / (p + 1)) + 1e-6);
 }
 
+/* Step factor and order after an accepted step at order q (Sec. 2: the
+ * next step size, and the order, are selected from the error estimates).
+ * Readings: eta_p = 1/((b_p ||E_p||)^(1/(p+1)) + 1e-6) with biases 6 for
+ * q-1 and q and 10 for q+1; the orders q-1 and q+1 are considered only
+ * when qwait == 0 (q+1 steps taken at q); ||E_{q-1}|| from the corrected
+ * z_q, ||E_{q+1}|| from the change of the scaled (q+1)th derivative since
+ * the saved correction ksave of step size h_ksave; no change below
+ * eta = 1.5; growth capped at etamax.  z is the corrected array, acor the
+ * correction Delta, dsm = C_q ||Delta||; tmp2 is scratch [n].  Returns eta,
+ * the order in *newq. */
+static double choose_step(int n, int q, int qmax, int qwait, const double *z, const double *acor,
+                          const double *w, const double *xi, const double *l, double dsm,
+                          int have_ksave, const double *ksave, double h, double h_ksave,
+                          double etamax, double *tmp2, int *newq_out)
+{
+    const double l1 = l[1];
+    double eta = eta_from(dsm, q, 6.0);
+    int newq = q;
+    const double kfac = l1 * l[q] / (1.0 + l1 * xi[q]);
+    if (qwait == 0) {
+        double em = 0.0, ep = 0.0;
+        if (q > 1) {
+            double l1m = 0.0, pm = 1.0;
+            for (int i = 0; i < q - 1; ++i) { l1m += 1.0 / xi[i]; pm *= xi[i]; }
+            em = eta_from(wrms(n, z + q * n, w) * pm / l1m, q - 1, 6.0);
+        }
+        if (q < qmax && have_ksave) {
+            double rq = pow(h / h_ksave, q + 1), pp = 1.0, l1p = l1 + 1.0 / xi[q];
+            for (int i = 0; i <= q; ++i) pp *= xi[i];
+            for (int i = 0; i < n; ++i) tmp2[i] = (kfac * acor[i] - rq * ksave[i]) / (q + 2);
+            ep = eta_from(wrms(n, tmp2, w) * pp / l1p, q + 1, 10.0);
+        }
+        if (em > eta && em >= ep) { eta = em; newq = q - 1; }
+        else if (ep > eta) { eta = ep; newq = q + 1; }
+    }
+    if (eta < 1.5) { eta = 1.0; newq = q; }
+    else eta = fmin(eta, etamax);
+    *newq_out = newq;
+    return eta;
+}
+
 /* The linear solve of the inexact Newton iteration (solution approaches
  * 1A/1B of Table 1; Eqs. linear and stop_linear, Sec. 2): GMRES on the
  * system scaled by S = diag(w) and unpreconditioned,
@@ -384,6 +425,69 @@ EXPORT int orc_gmres(const orc_problem *pb, long cell, const double *y, const do
     return gmres_solve(pb, cell, y, fy, w, gamma, tol, b, nfe);
 }
 
+/* One modified Newton solve of the corrector equation (Sec. 2):
+ *   G(y) = y - gamma f(t_n, y) - a_n = 0,  a_n = z0 - z1/l_1,
+ * from the prediction y = z0, written for the correction acor = y - z0 as
+ * delta = M^-1 ((h f(y) - z1)/l_1 - acor) with the factors of
+ * M = I - gamma_M J (or GMRES for the inexact iteration); a stale matrix
+ * (gamma != gamma_M) scales each correction by 2/(1 + gamma/gamma_M).
+ * Stopping test of Eq. stop_newton: after correction m,
+ *   R = max(c_r R, ||delta_m|| / ||delta_{m-1}||)  (c_r = 0.3, R = 1 at m = 0)
+ *   converged when R ||delta_m|| < c_eps eps = 0.1 / C_q  (WRMS norms);
+ * at most 3 corrections; divergence when ||delta_m|| > 2 ||delta_{m-1}||.
+ * Returns 1 on convergence; acor and ycur hold the last iterate, f and del
+ * the last f and correction; nfe and nni count f evaluations and
+ * iterations; *iters (nullable) receives the number of corrections. */
+static int newton_solve(const orc_problem *pb, long cell, const double *z, double h, double l1,
+                        double gamma, double gamma_M, double Cq, const double *M, const int32_t *piv,
+                        int krylov, const double *w, double *acor, double *ycur, double *f, double *del,
+                        int32_t *nfe, int32_t *nni, int *iters)
+{
+    const int n = pb->n;
+    int conv = 0, m;
+    for (int i = 0; i < n; ++i) { acor[i] = 0.0; ycur[i] = z[i]; }
+    double delp = 0.0, R = 1.0;
+    for (m = 0;; ++m) {
+        rhs_r(pb, cell, ycur, f);
+        (*nfe)++; (*nni)++;
+        for (int i = 0; i < n; ++i) del[i] = (h * f[i] - z[n + i]) / l1 - acor[i];
+        if (krylov) {
+            /* Eq. stop_linear: c_l = 0.05 of the Newton tolerance 0.1/C_q,
+             * a WRMS bound, i.e. sqrt(n) times it in the scaled 2-norm */
+            gmres_solve(pb, cell, ycur, f, w, gamma, 0.05 * (0.1 / Cq) * sqrt((double)n), del, nfe);
+        } else {
+            orc_lu_solve(n, M, piv, del);
+        }
+        if (gamma != gamma_M) {
+            double c = 2.0 / (1.0 + gamma / gamma_M);
+            for (int i = 0; i < n; ++i) del[i] *= c;
+        }
+        for (int i = 0; i < n; ++i) { acor[i] += del[i]; ycur[i] = z[i] + acor[i]; }
+        double dn = wrms(n, del, w);
+        if (!isfinite(dn)) break;
+        if (m > 0) R = fmax(0.3 * R, dn / delp);
+        if (R * dn * Cq < 0.1) { conv = 1; break; }  /* Eq. stop_newton */
+        if (m + 1 == 3 || (m > 0 && dn > 2.0 * delp)) break;
+        delp = dn;
+    }
+    if (iters) *iters = m + 1;
+    return conv;
+}
+
+/* newton_solve for tests, with given factors of M (LU only): z [2, n]
+ * (prediction z0 and z1), weights w; acor and y receive the last iterate,
+ * *iters the number of corrections; returns 1 on convergence. */
+EXPORT int orc_newton_solve(const orc_problem *pb, long cell, const double *z, double h, double l1,
+                            double gamma, double gamma_M, double Cq, const double *M,
+                            const int32_t *piv, const double *w, double *acor, double *y, int *iters)
+{
+    const int n = pb->n;
+    double f[n], del[n];
+    int32_t nfe = 0, nni = 0;
+    return newton_solve(pb, cell, z, h, l1, gamma, gamma_M, Cq, M, piv, 0, w, acor, y, f, del,
+                        &nfe, &nni, iters);
+}
+
 /* Matrix set-up: J at (t, y), M = I - gamma J, LU. Returns 0 on success. */
 static int setup_matrix(const orc_problem *pb, long cell, const double *y,
                         const double *w, int jac_mode, double gamma,
@@ -432,11 +536,15 @@ static double initial_step(const orc_problem *pb, long cell, double t0, double t
  *                              order increase decided after the step)
  * Record layout (doubles): y_n [n], P [6][6] (row = output column,
  * column = input column), c [6], gamma, 1/l_1, q, q_out (highest column of
- * Z_n).  Step sizes and orders are frozen; each corrector counts as solved
- * exactly (implicit function theorem with the exact Jacobian). */
-#define TAPE_R(n) ((n) + 46)
+ * Z_n), then the control decisions of the step: h_n and the numbers of
+ * Newton and error-test failures of its rejected attempts.  Step sizes and
+ * orders are frozen; each corrector counts as solved exactly (implicit
+ * function theorem with the exact Jacobian).  have_states: the records'
+ * y_n are states of a forward run (0 for a map built from decisions alone,
+ * whose replay starts each Newton solve from the prediction). */
+#define TAPE_R(n) ((n) + 49)
 typedef struct {
-    int n, cap, count, overflow;
+    int n, cap, count, overflow, have_states;
     double h0;
     double *y0;     /* [n] */
     double *rec;    /* [cap][TAPE_R(n)] */
@@ -466,19 +574,23 @@ static void tape_decrease(orc_tape *tp, int q, const double *nodes)
 }
 
 static void tape_record(orc_tape *tp, const double *y, const double *c, double gamma,
-                        double il1, int q, int q_out)
+                        double il1, int q, int q_out, double h, int ncf, int nef)
 {
     if (!tp) return;
     if (tp->count >= tp->cap) { tp->overflow = 1; return; }
     const int n = tp->n;
     double *r = tp->rec + (size_t)tp->count * TAPE_R(n);
-    memcpy(r, y, sizeof(double) * n);
+    if (y) memcpy(r, y, sizeof(double) * n);
+    else memset(r, 0, sizeof(double) * n);
     memcpy(r + n, tp->P, sizeof(double) * 36);
     memcpy(r + n + 36, c, sizeof(double) * 6);
     r[n + 42] = gamma;
     r[n + 43] = il1;
     r[n + 44] = q;
     r[n + 45] = q_out;
+    r[n + 46] = h;
+    r[n + 47] = ncf;
+    r[n + 48] = nef;
     tp->count++;
 }
 
@@ -502,7 +614,7 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
     double t = t0, h = 0.0;
     int q = 1, qwait = 2, have_M = 0, force_setup = 1, nst_lastsetup = 0;
     int have_ksave = 0;
-    double hist[QMAX + 1] = {0}, gamma_M = 0.0, R = 1.0, etamax = 1e4, h_ksave = 0.0;
+    double hist[QMAX + 1] = {0}, gamma_M = 0.0, etamax = 1e4, h_ksave = 0.0;
 
     if (!(tout > t0)) goto done_copy;
     memcpy(z, y, sizeof(double) * n);
@@ -551,33 +663,8 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
             for (;;) {  /* Newton on G(y) = y - gamma f(tn, y) - a_n, a_n = z0 - z1/l1 */
                 conv = 0;
                 if (!have_M) break;
-                for (int i = 0; i < n; ++i) { acor[i] = 0.0; ycur[i] = z[i]; }
-                double delp = 0.0;
-                R = 1.0;
-                for (int m = 0;; ++m) {
-                    rhs_r(pb, cell, ycur, f);
-                    s.nfe++; s.nni++;
-                    for (int i = 0; i < n; ++i) del[i] = (h * f[i] - z[n + i]) / l1 - acor[i];
-                    if (krylov) {
-                        /* Eq. stop_linear: c_l = 0.05 of the Newton tolerance 0.1/C_q,
-                         * a WRMS bound, i.e. sqrt(n) times it in the scaled 2-norm */
-                        gmres_solve(pb, cell, ycur, f, w, gamma, 0.05 * (0.1 / Cq) * sqrt((double)n),
-                                    del, &s.nfe);
-                    } else {
-                        orc_lu_solve(n, M, piv, del);
-                    }
-                    if (gamma != gamma_M) {
-                        double c = 2.0 / (1.0 + gamma / gamma_M);
-                        for (int i = 0; i < n; ++i) del[i] *= c;
-                    }
-                    for (int i = 0; i < n; ++i) { acor[i] += del[i]; ycur[i] = z[i] + acor[i]; }
-                    double dn = wrms(n, del, w);
-                    if (!isfinite(dn)) break;
-                    if (m > 0) R = fmax(0.3 * R, dn / delp);
-                    if (R * dn * Cq < 0.1) { conv = 1; break; }  /* Eq. stop_newton */
-                    if (m + 1 == 3 || (m > 0 && dn > 2.0 * delp)) break;
-                    delp = dn;
-                }
+                conv = newton_solve(pb, cell, z, h, l1, gamma, gamma_M, Cq, M, piv, krylov, w,
+                                    acor, ycur, f, del, &s.nfe, &s.nni, NULL);
                 if (conv || fresh) break;
                 /* stale matrix: rebuild at the predicted state and retry */
                 have_M = setup_matrix(pb, cell, z, w, op->jac_mode, gamma, M, piv, tmp) == 0;
@@ -646,38 +733,20 @@ static int bdf_cell(const orc_problem *pb, long cell, double *y, double t0,
         double cvec[6] = {0, 0, 0, 0, 0, 0};
         for (int j = 0; j <= q; ++j) cvec[j] = l[j];
         if (last) {
-            tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, q);
+            tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, q, h, ncf, nef);
             break;
         }
 
         /* step size and order for the next step */
         qwait--;
-        const double l1 = l[1];
-        double eta = eta_from(dsm, q, 6.0);
-        int newq = q;
+        int newq;
         /* scaled (q+1)-th derivative estimate h^{q+1} y^{(q+1)}/(q+1)! */
-        const double kfac = l1 * l[q] / (1.0 + l1 * xi[q]);
-        if (qwait == 0) {
-            double em = 0.0, ep = 0.0;
-            if (q > 1) {
-                double l1m = 0.0, pm = 1.0;
-                for (int i = 0; i < q - 1; ++i) { l1m += 1.0 / xi[i]; pm *= xi[i]; }
-                em = eta_from(wrms(n, z + q * n, w) * pm / l1m, q - 1, 6.0);
-            }
-            if (q < qmax && have_ksave) {
-                double rq = pow(h / h_ksave, q + 1), pp = 1.0, l1p = l1 + 1.0 / xi[q];
-                for (int i = 0; i <= q; ++i) pp *= xi[i];
-                for (int i = 0; i < n; ++i) tmp2[i] = (kfac * acor[i] - rq * ksave[i]) / (q + 2);
-                ep = eta_from(wrms(n, tmp2, w) * pp / l1p, q + 1, 10.0);
-            }
-            if (em > eta && em >= ep) { eta = em; newq = q - 1; }
-            else if (ep > eta) { eta = ep; newq = q + 1; }
-        }
-        if (eta < 1.5) { eta = 1.0; newq = q; }
-        else eta = fmin(eta, etamax);
+        const double kfac = l[1] * l[q] / (1.0 + l[1] * xi[q]);
+        double eta = choose_step(n, q, qmax, qwait, z, acor, w, xi, l, dsm, have_ksave, ksave, h, h_ksave,
+                                 etamax, tmp2, &newq);
         if (newq == q + 1)
             for (int j = 1; j <= q + 1; ++j) cvec[j] += l[j - 1] / xi[q];
-        tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, newq == q + 1 ? q + 1 : q);
+        tape_record(tp, z, cvec, h / l[1], 1.0 / l[1], q, newq == q + 1 ? q + 1 : q, h, ncf, nef);
         if (tp) tape_reset_map(tp);
         if (newq == q + 1) orc_order_increase(q, n, z, acor, l, xi[q]);
         else if (newq == q - 1) { orc_order_decrease(q, n, z, xi); tape_decrease(tp, q, xi); }
@@ -939,6 +1008,7 @@ EXPORT orc_tape *orc_tape_new(int n, int cap)
     orc_tape *tp = calloc(1, sizeof(orc_tape));
     tp->n = n;
     tp->cap = cap;
+    tp->have_states = 1;
     tp->y0 = calloc((size_t)n, sizeof(double));
     tp->rec = calloc((size_t)cap * TAPE_R(n), sizeof(double));
     tape_reset_map(tp);
@@ -961,6 +1031,16 @@ EXPORT int orc_tape_map(const orc_tape *tp, int r, double *P)
     if (r < 0 || r >= tp->count) return -1;
     memcpy(P, tp->rec + (size_t)r * TAPE_R(tp->n) + tp->n, sizeof(double) * 36);
     return 0;
+}
+
+/* The tape's contents for tests: h0 and y0 [n] into head [1 + n], the
+ * records [count][n + 49] into rec (layout above); returns count. */
+EXPORT int orc_tape_records(const orc_tape *tp, double *head, double *rec)
+{
+    head[0] = tp->h0;
+    memcpy(head + 1, tp->y0, sizeof(double) * tp->n);
+    memcpy(rec, tp->rec, sizeof(double) * (size_t)tp->count * TAPE_R(tp->n));
+    return tp->count;
 }
 
 EXPORT int orc_forward_tape(const orc_problem *pb, long cell, double *y, double t0, double tout,
@@ -1086,7 +1166,8 @@ static int replay(const orc_problem *pb, long cell, const orc_tape *tp, double *
         for (int k = 0; k < q; ++k)
             for (int j = q; j > k; --j)
                 for (int i = 0; i < n; ++i) Zp[(j - 1) * n + i] += Zp[j * n + i];
-        memcpy(y, rec, sizeof(double) * n);        /* the recorded state is the first guess */
+        if (tp->have_states) memcpy(y, rec, sizeof(double) * n);   /* the recorded state */
+        else memcpy(y, Zp, sizeof(double) * n);                  /* the prediction */
         for (int it = 0; it < 60; ++it) {
             rhs_r(pb, cell, y, f);
             for (int i = 0; i < n; ++i) g[i] = -(y[i] - gamma * f[i] - (Zp[i] - il1 * Zp[n + i]));
@@ -1117,6 +1198,213 @@ static int replay(const orc_problem *pb, long cell, const orc_tape *tp, double *
 EXPORT int orc_replay_tape(const orc_problem *pb, long cell, const orc_tape *tp, double *yout)
 {
     return replay(pb, cell, tp, yout, NULL);
+}
+
+/* replay, with the exact state of every step in ys [count, n] */
+EXPORT int orc_replay_tape_states(const orc_problem *pb, long cell, const orc_tape *tp, double *yout,
+                                  double *ys)
+{
+    return replay(pb, cell, tp, yout, ys);
+}
+
+/* ---- a step history given by its control decisions ---------------------
+ * The frozen map of a cell's accepted steps rebuilt from the decisions of
+ * the adaptive step and order selection alone (Sec. 2): the starting step
+ * h0 and, per accepted step n, its size h_n, its order q_n, the order
+ * q_out,n of the array after it (q_n + 1 after an order increase) and the
+ * Newton and error-test failures of its rejected attempts.  Everything
+ * else is computed here, from the oracle's own coefficient algebra:
+ *  - the column map P_n: the order decreases from q_out,n-1 down to q_n,
+ *    each keeping the polynomial's values at the current time and at the
+ *    previous accepted times (nodes in units of h_{n-1}), then the rescale
+ *    of columns 1..q_n by h_n/h_{n-1};
+ *  - xi, l, gamma = h_n/l_1, 1/l_1 and the update vector c_n (l, plus the
+ *    terms of an order increase, l_{j-1}/xi_{q+1}).
+ * Reading: rescales and order decreases both keep one polynomial in t (a
+ * rescale changes only its variable, a decrease keeps its values at the
+ * current and previous accepted times), so the map does not depend on the
+ * order in which an integrator applied them between two accepted steps,
+ * or on the step sizes of its rejected attempts.  ys (nullable,
+ * [count, n]) are states stored with the records (a forward run's, to
+ * follow it); without them the replay starts each Newton solve from the
+ * prediction. */
+EXPORT orc_tape *orc_tape_from_decisions(int n, int count, const double *y0, double h0,
+                                         const double *h, const int32_t *q, const int32_t *qo,
+                                         const int32_t *ncf, const int32_t *nef, const double *ys)
+{
+    orc_tape *tp = orc_tape_new(n, count > 0 ? count : 1);
+    memcpy(tp->y0, y0, sizeof(double) * n);
+    tp->h0 = h0;
+    tp->have_states = ys != NULL;
+    double hist[QMAX + 1] = {0}, hprev = h0;
+    int qprev = 1;                            /* [y0, h0 f(y0)] is of order 1 */
+    for (int r = 0; r < count; ++r) {
+        if (q[r] < 1 || q[r] > QMAX || q[r] > qprev || qo[r] < q[r] || qo[r] > q[r] + 1 ||
+            !(h[r] > 0.0)) {
+            orc_tape_free(tp);
+            return NULL;
+        }
+        tape_reset_map(tp);
+        if (q[r] < qprev) {
+            double nodes[QMAX], sacc = 0.0;
+            for (int i = 0; i < QMAX; ++i) { sacc += hist[i]; nodes[i] = sacc / hprev; }
+            for (int k = qprev; k > q[r]; --k) tape_decrease(tp, k, nodes);
+        }
+        tape_rescale(tp, q[r], h[r] / hprev);
+        double xi[QMAX + 2], l[QMAX + 2], cvec[6] = {0, 0, 0, 0, 0, 0};
+        bdf_xi(q[r] + 1, h[r], hist, xi);
+        orc_bdf_l(q[r], xi, l);
+        for (int j = 0; j <= q[r]; ++j) cvec[j] = l[j];
+        if (qo[r] == q[r] + 1)
+            for (int j = 1; j <= q[r] + 1; ++j) cvec[j] += l[j - 1] / xi[q[r]];
+        tape_record(tp, ys ? ys + (size_t)r * n : NULL, cvec, h[r] / l[1], 1.0 / l[1], q[r], qo[r], h[r],
+                    ncf ? ncf[r] : 0, nef ? nef[r] : 0);
+        for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
+        hist[0] = h[r];
+        hprev = h[r];
+        qprev = qo[r];
+    }
+    return tp;
+}
+
+/* Corrector y - gamma f(y) - (z0 - il1 z1) = 0 solved by full Newton
+ * (complex-step Jacobian every iteration) from the guess in y, to
+ * |delta_i| <= 1e-13 |y_i| + 1e-30.  Returns 0, or -2 on a singular matrix. */
+static int exact_corrector(const orc_problem *pb, long cell, const double *Zp, double gamma, double il1,
+                           double *y)
+{
+    const int n = pb->n;
+    double f[n], g[n], J[n * n], w1[n];
+    int32_t piv[n];
+    for (int i = 0; i < n; ++i) w1[i] = 1.0;
+    for (int it = 0; it < 60; ++it) {
+        rhs_r(pb, cell, y, f);
+        for (int i = 0; i < n; ++i) g[i] = -(y[i] - gamma * f[i] - (Zp[i] - il1 * Zp[n + i]));
+        orc_jac(pb, cell, y, f, w1, 0, J);
+        for (int i = 0; i < n * n; ++i) J[i] = -gamma * J[i];
+        for (int i = 0; i < n; ++i) J[i * n + i] += 1.0;
+        if (orc_lu_factor(n, J, piv)) return -2;
+        orc_lu_solve(n, J, piv, g);
+        int done = 1;
+        for (int i = 0; i < n; ++i) {
+            y[i] += g[i];
+            if (fabs(g[i]) > 1e-13 * fabs(y[i]) + 1e-30) done = 0;
+        }
+        if (done) break;
+    }
+    return 0;
+}
+
+/* Following a forward run through its recorded states and decisions (a
+ * tape from orc_tape_from_decisions with ys; Sec. 2, Eq. wrms,
+ * Eq. stop_newton).  The Nordsieck array is advanced with this oracle's own
+ * maps, prediction and coefficients, taking the recorded y_n as each
+ * step's corrector solution (Z_n = Z_pred + c_n (y_n - z0_pred)), and at
+ * every step the oracle evaluates the integrator's decisions itself, with
+ * weights w_i = 1/(rtol |y_{n-1,i}| + atol_i):
+ *   out[0] dsm = C_q ||y_n - z0_pred||    the error test (accepted iff < 1)
+ *   out[1]       C_q ||y_n - y*||         y* the exact corrector (full
+ *                                          Newton): the accepted iterate's
+ *                                          distance from it, in the units
+ *                                          of the Newton test (0.1 there)
+ *   out[2] eta, out[3] order               chosen after the step (choose_step)
+ *   out[4] h_{n+1}/h_n                     recorded, where it shows that choice
+ *                                          (next step not the last and
+ *                                          without failures), else NaN
+ *   out[5] the recorded order choice       an increase on the record, or the
+ *                                          next step's order when it had no
+ *                                          failures, else NaN
+ *   out[6] C_q ||y* - z0_pred||           the error test of an exact corrector
+ *   out[7] eta_q of that test              (the same-order step factor)
+ *   out[8] 1 where orders q-1 and q+1 were considered (qwait = 0), else 0
+ *   out[9] the step's rejected attempts (Newton and error-test failures)
+ * out has 10 doubles per step (NaN in 2..5 for the last step, which makes
+ * no choice).  The counter qwait follows the record: an increase (q_out)
+ * or a choice made at qwait = 0 restarts it at the new order + 1, an order
+ * decrease seen at the next step (at its accept or in a failure) restarts it
+ * at that order + 1, a third error-test failure at 2.  Returns 0, or -2 if
+ * an exact corrector fails. */
+EXPORT int orc_follow_tape(const orc_problem *pb, long cell, const orc_tape *tp, double rtol,
+                           const double *atol, int max_order, double *out)
+{
+    const int n = pb->n, R = TAPE_R(n), count = tp->count;
+    const int qmax = max_order < 1 ? 1 : (max_order > QMAX ? QMAX : max_order);
+    double *Z = calloc(6 * (size_t)n, sizeof(double)), *Zp = calloc(6 * (size_t)n, sizeof(double));
+    double *w = malloc(sizeof(double) * n), *d = malloc(sizeof(double) * n);
+    double *ystar = malloc(sizeof(double) * n), *tmp2 = malloc(sizeof(double) * n);
+    double *ksave = calloc((size_t)n, sizeof(double)), *f = malloc(sizeof(double) * n);
+    double *zc = calloc(6 * (size_t)n, sizeof(double));
+    int rc = 0, qwait = 2, have_ks = 0;
+    double h_ks = 0.0;
+    memcpy(Z, tp->y0, sizeof(double) * n);
+    rhs_r(pb, cell, tp->y0, f);
+    for (int i = 0; i < n; ++i) Z[n + i] = tp->h0 * f[i];
+    for (int r = 0; r < count && rc == 0; ++r) {
+        const double *rec = tp->rec + (size_t)r * R;
+        const double *P = rec + n, *c = rec + n + 36;
+        const double gamma = rec[n + 42], il1 = rec[n + 43], h = rec[n + 46];
+        const int q = (int)rec[n + 44], qo = (int)rec[n + 45];
+        const int fails = (int)rec[n + 47] + (int)rec[n + 48];
+        const int qin = r > 0 ? (int)tp->rec[(size_t)(r - 1) * R + n + 45] : 1;
+        double *o = out + (size_t)r * 10;
+        if ((int)rec[n + 48] >= 3) { qwait = 2; have_ks = 0; }
+        else if (q < qin) qwait = q + 1;
+        set_weights(n, Z, rtol, atol, w);                 /* from y_{n-1} */
+        for (int a = 0; a < 6; ++a)
+            for (int i = 0; i < n; ++i) {
+                double sacc = 0.0;
+                for (int b = 0; b < 6; ++b) sacc += P[a * 6 + b] * Z[b * n + i];
+                Zp[a * n + i] = sacc;
+            }
+        predict(q, n, Zp);
+        double xi[QMAX + 2], l[QMAX + 2], hist[QMAX + 1] = {0};
+        for (int k = 0; k < QMAX && k < r; ++k) hist[k] = tp->rec[(size_t)(r - 1 - k) * R + n + 46];
+        bdf_xi(q + 1, h, hist, xi);
+        orc_bdf_l(q, xi, l);
+        const double Cq = error_constant(l[1], xi[q]);
+        for (int i = 0; i < n; ++i) d[i] = rec[i] - Zp[i];     /* Delta of the recorded state */
+        o[0] = Cq * wrms(n, d, w);
+        memcpy(ystar, Zp, sizeof(double) * n);
+        if (exact_corrector(pb, cell, Zp, gamma, il1, ystar)) { rc = -2; break; }
+        for (int i = 0; i < n; ++i) tmp2[i] = rec[i] - ystar[i];
+        o[1] = Cq * wrms(n, tmp2, w);
+        for (int i = 0; i < n; ++i) tmp2[i] = ystar[i] - Zp[i];
+        o[6] = Cq * wrms(n, tmp2, w);
+        o[7] = eta_from(o[6], q, 6.0);
+        o[9] = fails;
+        /* the corrected array (for the order q-1 estimate), then the choice */
+        for (int j = 0; j <= q; ++j)
+            for (int i = 0; i < n; ++i) zc[j * n + i] = Zp[j * n + i] + l[j] * d[i];
+        if (r == count - 1) {
+            o[2] = o[3] = o[4] = o[5] = NAN;
+            o[8] = 0.0;
+        } else {
+            qwait--;
+            const double etamax = fails ? 1.0 : (r == 0 ? 1e4 : 10.0);
+            int newq;
+            o[2] = choose_step(n, q, qmax, qwait, zc, d, w, xi, l, o[0], have_ks, ksave, h, h_ks, etamax,
+                               tmp2, &newq);
+            o[3] = newq;
+            o[8] = qwait == 0;
+            const double *nx = tp->rec + (size_t)(r + 1) * R;
+            const int nfail = (int)nx[n + 47] + (int)nx[n + 48];
+            o[4] = (nfail == 0 && r + 1 < count - 1) ? nx[n + 46] / h : NAN;
+            o[5] = qo == q + 1 ? (double)(q + 1) : (nfail == 0 ? nx[n + 44] : NAN);
+            /* the counter as the integrator leaves it (the recorded choice) */
+            if (qo == q + 1 || qwait == 0) { qwait = qo + 1; have_ks = 0; }
+            if (qwait == 1 && q < qmax) {
+                const double kfac = l[1] * l[q] / (1.0 + l[1] * xi[q]);
+                for (int i = 0; i < n; ++i) ksave[i] = kfac * d[i];
+                h_ks = h; have_ks = 1;
+            }
+        }
+        /* Z_n = Z_pred + c (y_n - z0_pred), columns above q_out zero */
+        for (int j = 0; j < 6; ++j)
+            for (int i = 0; i < n; ++i)
+                Z[j * n + i] = (j <= qo) ? ((j <= q ? Zp[j * n + i] : 0.0) + c[j] * d[i]) : 0.0;
+    }
+    free(Z); free(Zp); free(w); free(d); free(ystar); free(tmp2); free(ksave); free(f); free(zc);
+    return rc;
 }
 
 /* Squared-error loss sum_k (Y_k - target_k)^2 at the replayed final state,

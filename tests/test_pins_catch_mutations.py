@@ -88,6 +88,17 @@ MUTATIONS = [
      "grad[2 * j + 1] += -scale * d / (ORC_RC * T);", "grad[2 * j + 1] += scale * d / (ORC_RC * T);"),
     ("order decrease subtracting the wrong multiple", "oracle.c",
      "z[j * n + k] -= e[j - 1] * z[q * n + k];", "z[j * n + k] -= e[j] * z[q * n + k];"),
+    ("Newton rate estimate taken as a minimum", "oracle.c",
+     "if (m > 0) R = fmax(0.3 * R, dn / delp);", "if (m > 0) R = fmin(0.3 * R, dn / delp);"),
+    ("Newton rate estimate with c_r = 0.5", "oracle.c",
+     "if (m > 0) R = fmax(0.3 * R, dn / delp);", "if (m > 0) R = fmax(0.5 * R, dn / delp);"),
+    ("adjoint of the column map applied untransposed", "oracle.c",
+     "for (int o = 0; o < 6; ++o) s += P[o * 6 + a] * lam[o * n + i];",
+     "for (int o = 0; o < 6; ++o) s += P[a * 6 + o] * lam[o * n + i];"),
+    ("decision map rescaled by the inverse step ratio", "oracle.c",
+     "tape_rescale(tp, q[r], h[r] / hprev);", "tape_rescale(tp, q[r], hprev / h[r]);"),
+    ("following a run without restarting the order counter", "oracle.c",
+     "if (qo == q + 1 || qwait == 0) { qwait = qo + 1; have_ks = 0; }", "if (qo == q + 1) { qwait = qo + 1; have_ks = 0; }"),
 ]
 
 
