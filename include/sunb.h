@@ -107,14 +107,14 @@ typedef struct {
 
 /* Totals over all cells of the last sunb_integrate (the work counters the
  * paper uses as cost measures, Sec. 4.1.1 and 4.1.5). */
-typedef struct {
+typedef struct sunb_stats_t {
     int64_t nst, nfe, nje, nni, ncf, nef;   /* steps, f evals, Newton-matrix
                                                builds, Newton iterations,
                                                Newton failures, error-test failures */
     int32_t max_nst;          /* largest per-cell step count                 */
     int32_t worst_status;     /* most negative per-cell status               */
     int64_t n_failed;         /* cells with a nonzero status                 */
-} sunb_totals;
+} sunb_stats_t;
 
 /* Create a context: validates the problem, copies the tables to the device
  * and allocates all workspace once (the pooled-memory lesson of Sec. 4.3.1:
@@ -198,17 +198,23 @@ int sunb_set_linear_solver(sunb_ctx *ctx, int solver);
 #define SUNB_METHOD_ERK 1
 int sunb_set_method(sunb_ctx *ctx, int method);
 
-/* Per-cell parameters, a device array [C, P] in the layout of sunb_kind
- * (SUNB_MIXED: the cosmology cells' (rho, F) pairs, then the mechanism
- * cells' pressures).  The pointer is kept, not copied: it must stay valid
- * while integrations that use it are in flight. */
-int sunb_set_params(sunb_ctx *ctx, const double *dev_params);
+/* Per-cell parameters p_c of y_c' = f(t, y_c; p_c) (Sec. 2, Eq. 1; for
+ * chemistry the cell's pressure, Sec. 3.1; for heating-cooling its density
+ * and forcing, Sec. 3.2): a caller-owned device array [C, P] of doubles in
+ * the layout of sunb_kind (SUNB_MIXED: the cosmology cells' (rho, F) pairs,
+ * then the mechanism cells' pressures).  bytes is the array's size and must
+ * equal 8 * C * P for the context's cells (3 per Robertson cell, 1 per
+ * mechanism cell, 2 per cosmology cell); any other value returns
+ * SUNB_ILL_INPUT and keeps the previous array.  The pointer is kept, not
+ * copied: it must stay valid while integrations that use it are in
+ * flight. */
+int sunb_set_params(sunb_ctx *ctx, const double *dev_params, size_t bytes);
 
 /* Advance every cell from t0 to tout (one outer step dt_CFD; Sec. 2) in
  * place in dev_y [C, N].  Each call is a cold start at order 1 and lands
  * exactly on tout.  dev_status (nullable, int32 [C]) receives per-cell
  * statuses; a cell that fails keeps its last accepted state.  Asynchronous:
- * the return value only reports launch problems; see sunb_get_totals. */
+ * the return value only reports launch problems; see sunb_stats. */
 int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t *dev_status);
 
 /* Same from host memory: copies host_y [C, N] to a library buffer,
@@ -216,10 +222,16 @@ int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t
  * nullable.  Returns the most negative per-cell status. */
 int sunb_integrate_host(sunb_ctx *ctx, double *host_y, double t0, double tout, int32_t *host_status);
 
-/* Waits for the stream, then fills *host_totals (nullable) and copies the
- * per-cell counters to dev_cell_stats (nullable, int32 [C, 8]: nst, nfe,
- * nje, nni, ncf, nef, last order, status).  Returns the worst status. */
-int sunb_get_totals(sunb_ctx *ctx, sunb_totals *host_totals, int32_t *dev_cell_stats);
+/* Work counters of the last sunb_integrate, the paper's cost measures
+ * (steps, right-hand sides, Jacobians, Newton iterations and failures;
+ * Sec. 4.1.1, 4.1.5) and its statuses (Sec. 2: a cell that fails keeps its
+ * last accepted state).  Waits for the context's stream, then fills
+ * *host_totals (nullable; sums over all cells) and copies the per-cell
+ * counters to dev_per_cell (nullable, caller-owned device int32 [C, 8]:
+ * nst, nfe, nje, nni, ncf, nef, last order, status; for SUNB_MIXED the
+ * cosmology cells first).  Returns the most negative per-cell status, or a
+ * CUDA failure as SUNB_CUDA_ERROR. */
+int sunb_stats(sunb_ctx *ctx, sunb_stats_t *host_totals, int32_t *dev_per_cell);
 
 /* Evaluate the right-hand side f(y) for n_cells cells (step a5 on its own):
  * dev_y, dev_f [n_cells, N], cell c uses parameters of cell c. */
@@ -282,6 +294,28 @@ int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final);
  * Returns SUNB_NO_RECORD for a context without tapes. */
 int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double *dev_grad_cells);
 
+/* The recorded step history (a context with record_adjoint = cap > 0):
+ * copies the tapes of cells first_cell .. first_cell + n_cells - 1 into
+ * host_out (caller-owned host memory, n_cells * sunb_tape_stride(ctx)
+ * doubles) and waits for the stream.  Per cell, with N unknowns and
+ * R = N + 49: a header of 8 + N doubles [count, h0, overflow (0 or 1),
+ * 5 unused, y0 (N)], then cap records of R doubles, of which the first
+ * count hold the accepted steps in order: y_n (N; the forward run's
+ * state, or the exact corrector's after sunb_adjoint_replay), the column
+ * map P (6 x 6, row = output Nordsieck column, applied to the previous
+ * step's array: rescales and order decreases), the update vector c (6),
+ * gamma, 1/l_1, q (the step's order), q_out (the order of the array after
+ * the step: q + 1 after an order increase), h_n (the step size), and the
+ * Newton and error-test failures of the step's rejected attempts.  These
+ * are the control decisions of Sec. 2's adaptive step and order
+ * selection (Eq. wrms, Eq. stop_newton), exported so that they can be
+ * replayed.  SUNB_NO_RECORD without tapes; SUNB_ILL_INPUT for a range
+ * outside the cells. */
+int sunb_get_tapes(sunb_ctx *ctx, int64_t first_cell, int64_t n_cells, double *host_out);
+
+/* Doubles per cell of sunb_get_tapes' output (0 without tapes). */
+int64_t sunb_tape_stride(const sunb_ctx *ctx);
+
 /* Replace the Arrhenius parameters ln A_j and Ea_j (host arrays [M]) of a
  * mechanism context; synchronises the context's stream. */
 int sunb_set_arrhenius(sunb_ctx *ctx, const double *host_lnA, const double *host_Ea);
@@ -337,6 +371,10 @@ int sunb_destroy(sunb_ctx *ctx);
  *    capture.  The counter is cleared on every call.
  *  - All calls share the array: calls whose work overlaps on the GPU (on
  *    different streams, or from several host threads) race; serialise them.
+ *  - The set-up is cached per device index for the life of the process: a
+ *    cudaDeviceReset (or anything else that destroys the device's primary
+ *    context) invalidates it, and calling this entry point on that device
+ *    afterwards is not supported.
  *  - Asynchronous on stream; returns launch errors only; errors are
  *    described by sunb_last_error(NULL). */
 int sunb_integrate_robertson_noalloc(const double *dev_k, double *dev_y, int64_t n_cells,

@@ -87,14 +87,14 @@ class _Totals(ctypes.Structure):
 SIGNATURES = {
     "sunb_create": (ctypes.c_int, [ctypes.POINTER(_Problem), _vp, ctypes.POINTER(_vp)]),
     "sunb_set_tolerances": (ctypes.c_int, [_vp, ctypes.c_double, ctypes.c_double, _dp]),
-    "sunb_set_params": (ctypes.c_int, [_vp, _vp]),
+    "sunb_set_params": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
     "sunb_set_typical_tolerances": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _dp]),
     "sunb_set_jacobian": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sunb_set_linear_solver": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sunb_set_method": (ctypes.c_int, [_vp, ctypes.c_int]),
     "sunb_integrate": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, _vp]),
     "sunb_integrate_host": (ctypes.c_int, [_vp, _dp, ctypes.c_double, ctypes.c_double, _ip]),
-    "sunb_get_totals": (ctypes.c_int, [_vp, ctypes.POINTER(_Totals), _vp]),
+    "sunb_stats": (ctypes.c_int, [_vp, ctypes.POINTER(_Totals), _vp]),
     "sunb_rhs": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
     "sunb_jac": (ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64]),
     "sunb_lu_solve_batched": (ctypes.c_int, [ctypes.c_int32, ctypes.c_int64, _vp, _vp, _vp, _vp, _vp]),
@@ -104,6 +104,8 @@ SIGNATURES = {
     "sunb_adjoint_replay": (ctypes.c_int, [_vp, _vp]),
     "sunb_adjoint": (ctypes.c_int, [_vp, _vp, _vp, _vp]),
     "sunb_set_arrhenius": (ctypes.c_int, [_vp, _dp, _dp]),
+    "sunb_get_tapes": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_int64, _dp]),
+    "sunb_tape_stride": (ctypes.c_int64, [_vp]),
     "sunb_graph_capture": (ctypes.c_int, [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.c_int32, _vp]),
     "sunb_graph_launch": (ctypes.c_int, [_vp, ctypes.c_double]),
     "sunb_get_lanes_per_cell": (ctypes.c_int, [_vp]),
@@ -155,6 +157,28 @@ def _ptr(t):
 
 def _cont(a, dtype):
     return np.ascontiguousarray(a, dtype=dtype)
+
+
+def _dev(t, dtype, shape, name, optional=False):
+    """Check that t is a contiguous CUDA tensor of the given dtype and
+    shape on the current device (None passes when optional); the library
+    receives a raw pointer, so a mismatch would read or write past t."""
+    import torch
+    if t is None:
+        if optional:
+            return None
+        raise TypeError(f"{name} must be a CUDA tensor, not None")
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor")
+    if t.dtype != dtype:
+        raise TypeError(f"{name} must be {dtype}, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    if t.device.index != torch.cuda.current_device():
+        raise ValueError(f"{name} is on {t.device}, not on the current device")
+    if tuple(t.shape) != tuple(shape):
+        raise ValueError(f"{name} must have shape {tuple(shape)}, got {tuple(t.shape)}")
+    return t
 
 
 class Integrator:
@@ -231,13 +255,32 @@ class Integrator:
         _check(lib().sunb_set_method(self.ctx, int(method)), self.ctx)
 
     def set_params(self, params):
-        """params: float64 CUDA tensor in the kind's layout (kept alive here)."""
+        """params: float64 CUDA tensor in the kind's layout (kept alive here);
+        its byte count is checked by the library against the context's cells."""
+        import torch
+        if not (isinstance(params, torch.Tensor) and params.is_cuda and params.dtype == torch.float64
+                and params.is_contiguous()):
+            raise TypeError("params must be a contiguous float64 CUDA tensor")
+        _check(lib().sunb_set_params(self.ctx, _ptr(params), params.numel() * 8), self.ctx)
         self._params = params
-        _check(lib().sunb_set_params(self.ctx, _ptr(params)), self.ctx)
 
     # -- integration
+    def _check_state(self, y, status):
+        """y: contiguous float64 CUDA tensor of n_cells * n_vars (+ cosmology
+        cells) values; status: None or contiguous int32 CUDA tensor, one per cell."""
+        import torch
+        _dev(y, torch.float64, y.shape, "y")
+        if y.numel() != self.n_cells * self.n_vars + self.n_cells_cosmo:
+            raise ValueError(f"y has {y.numel()} values, the context's cells need "
+                             f"{self.n_cells * self.n_vars + self.n_cells_cosmo}")
+        if status is not None:
+            _dev(status, torch.int32, status.shape, "status")
+            if status.numel() != self.n_cells + self.n_cells_cosmo:
+                raise ValueError("status needs one int32 per cell")
+
     def integrate(self, y, t0, tout, status=None):
         """In-place advance of the float64 CUDA tensor y from t0 to tout."""
+        self._check_state(y, status)
         _check(lib().sunb_integrate(self.ctx, _ptr(y), t0, tout, _ptr(status)), self.ctx)
 
     def integrate_host(self, y, t0, tout, status=None):
@@ -252,7 +295,7 @@ class Integrator:
 
     def totals(self, cell_stats=None):
         t = _Totals()
-        rc = lib().sunb_get_totals(self.ctx, ctypes.byref(t), _ptr(cell_stats))
+        rc = lib().sunb_stats(self.ctx, ctypes.byref(t), _ptr(cell_stats))
         if rc < -6:
             _check(rc, self.ctx)
         return {f: getattr(t, f) for f, _ in _Totals._fields_}
@@ -266,6 +309,7 @@ class Integrator:
     # -- CUDA graph of outer steps
     def graph_capture(self, y, t0, dt, nsteps, status=None):
         """Capture nsteps outer steps of length dt on y (kept by the graph)."""
+        self._check_state(y, status)
         self._graph_y = (y, status)
         _check(lib().sunb_graph_capture(self.ctx, _ptr(y), t0, dt, nsteps, _ptr(status)), self.ctx)
 
@@ -294,6 +338,31 @@ class Integrator:
             if per_cell else None
         _check(lib().sunb_adjoint(self.ctx, _ptr(dLdy.contiguous()), _ptr(g), _ptr(gc)), self.ctx)
         return (g, gc) if per_cell else g
+
+    def tapes(self, first_cell=0, n_cells=None):
+        """The recorded step histories of cells first_cell.. (a context with
+        record_adjoint): a list of dicts per cell with y0, h0, overflow and,
+        per accepted step, y (states), P (column maps [6, 6]), c, gamma, il1,
+        q, qo, h, ncf, nef (the control decisions)."""
+        n_cells = self.n_cells - first_cell if n_cells is None else n_cells
+        stride = lib().sunb_tape_stride(self.ctx)
+        if stride <= 0:
+            raise SunbError(-31, "context created without record_adjoint")
+        buf = np.empty((n_cells, stride), dtype=np.float64)
+        _check(lib().sunb_get_tapes(self.ctx, first_cell, n_cells, buf.ctypes.data_as(_dp)), self.ctx)
+        N = self.n_vars
+        R = N + 49
+        out = []
+        for row in buf:
+            count = int(row[0])
+            rec = row[8 + N:8 + N + count * R].reshape(count, R)
+            out.append(dict(count=count, h0=row[1], overflow=bool(row[2]), y0=row[8:8 + N].copy(),
+                            y=rec[:, :N].copy(), P=rec[:, N:N + 36].reshape(count, 6, 6).copy(),
+                            c=rec[:, N + 36:N + 42].copy(), gamma=rec[:, N + 42].copy(),
+                            il1=rec[:, N + 43].copy(), q=rec[:, N + 44].astype(np.int32),
+                            qo=rec[:, N + 45].astype(np.int32), h=rec[:, N + 46].copy(),
+                            ncf=rec[:, N + 47].astype(np.int32), nef=rec[:, N + 48].astype(np.int32)))
+        return out
 
     # -- single steps of the path
     def rhs(self, y, out=None):
@@ -380,6 +449,10 @@ def integrate_robertson_noalloc(k, y, t0, tout, rtol, atol, status=None, max_ste
     that may not allocate device memory): k, y float64 CUDA tensors [C, 3],
     y advanced in place; at most 65536 cells per call; calls that overlap on
     the GPU share one static scratch array and must not run concurrently."""
+    import torch
+    _dev(y, torch.float64, (y.shape[0] if y.dim() == 2 else -1, 3), "y")
+    _dev(k, torch.float64, tuple(y.shape), "k")
+    _dev(status, torch.int32, (y.shape[0],), "status", optional=True)
     a = _cont(np.broadcast_to(np.asarray(atol, dtype=np.float64), (3,)), np.float64)
     rc = lib().sunb_integrate_robertson_noalloc(_ptr(k), _ptr(y), y.shape[0], t0, tout, rtol,
                                                 a.ctypes.data_as(_dp), max_steps, _ptr(status),

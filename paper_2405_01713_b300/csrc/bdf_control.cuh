@@ -466,7 +466,7 @@ struct CellRun {
         for (int i = QMAX; i > 0; --i) hist[i] = hist[i - 1];
         hist[0] = h;
         if (last) {
-            c.rec_accept(q, q, l, 0.0, gamma, il1);
+            c.rec_accept(q, q, l, 0.0, gamma, il1, h, ncf, nef);
             finish(c);
             return;
         }
@@ -501,7 +501,7 @@ struct CellRun {
         }
         if (eta < ETA_THRESH) { eta = 1.0; newq = q; }
         else eta = fmin(eta, etamax);
-        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma, il1);
+        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma, il1, h, ncf, nef);
         if (newq == q + 1) c.order_increase(q, l, inv[q]);
         else if (newq == q - 1) {
             double e[QMAX + 1];

@@ -224,9 +224,10 @@ __device__ void lu_solve_t(const Grp<L> &g, const double *mat, int N, const int3
 // Header and record sizes (doubles) of a cell's adjoint tape: the header is
 // [count, h0, overflow, 5 spare, y0 (N)]; a record is y_n (N), the column
 // map P (6 x 6, row = output column), the update vector c (6), gamma, 1/l_1,
-// q, q_out.
+// q, q_out, then the step's control decisions: its size h_n and the Newton
+// and error-test failures of its attempts (ncf, nef).
 __host__ __device__ __forceinline__ int tape_header(int N) { return 8 + N; }
-__host__ __device__ __forceinline__ int tape_record(int N) { return N + 46; }
+__host__ __device__ __forceinline__ int tape_record(int N) { return N + 49; }
 
 // Krylov scratch of one lane group (global memory, doubles): the basis
 // [l+1][N], the Hessenberg matrix [l+1][l], the rotations cs and sn [l],
@@ -355,9 +356,9 @@ struct GroupCell : KrylovScratch<KRY> {
         if (tape) rec_init_body(h0);
     }
     __device__ __forceinline__ void rec_accept(int q, int qo, const double *l, double inv_xi, double gamma,
-                                               double il1)
+                                               double il1, double h, int ncf, int nef)
     {
-        if (tape) rec_accept_body(q, qo, l, inv_xi, gamma, il1);
+        if (tape) rec_accept_body(q, qo, l, inv_xi, gamma, il1, h, ncf, nef);
     }
     __device__ __noinline__ void rec_init_body(double h0)
     {
@@ -368,9 +369,10 @@ struct GroupCell : KrylovScratch<KRY> {
         rec_reset_map();
     }
     // one accepted step: y_n (= z0 after the correction), the map, the
-    // update vector (with the terms of an order increase), gamma, 1/l_1
+    // update vector (with the terms of an order increase), gamma, 1/l_1, and
+    // the step size and failed attempts of the step
     __device__ __noinline__ void rec_accept_body(int q, int qo, const double *l, double inv_xi, double gamma,
-                                                 double il1)
+                                                 double il1, double h, int ncf, int nef)
     {
         if (rec_count >= tape_cap) {
             if (g.lane == 0) tape[2] = 1.0;
@@ -393,6 +395,9 @@ struct GroupCell : KrylovScratch<KRY> {
             r[N + 43] = il1;
             r[N + 44] = (double)q;
             r[N + 45] = (double)qo;
+            r[N + 46] = h;
+            r[N + 47] = (double)ncf;
+            r[N + 48] = (double)nef;
             tape[0] = (double)(rec_count + 1);
         }
         ++rec_count;

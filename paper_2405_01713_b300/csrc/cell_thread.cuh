@@ -114,7 +114,7 @@ struct ThreadCell {
     double *yg;   // this cell's state in global memory
 
     __device__ __forceinline__ void rec_init(double) {}
-    __device__ __forceinline__ void rec_accept(int, int, const double *, double, double, double) {}
+    __device__ __forceinline__ void rec_accept(int, int, const double *, double, double, double, double, int, int) {}
 
     __device__ __forceinline__ void load_y(int s)
     {

@@ -1020,22 +1020,32 @@ static int autotune(sunb_ctx *ctx, const double *dev_y, double t0, double tout)
     const int startL = ctx->L, startc = ctx->cells_per_cta;
     int bestL = startL, bestc = startc;
     const int Ls[3] = {8, 16, 32};
+    // any failure inside a trial returns with the mapping it started from
+    auto restore = [&](int code) -> int {
+        const std::string why = ctx->err;
+        configure_mech(ctx, startL, startc);
+        ctx->err = why;
+        return code;
+    };
+    auto cu = [&](cudaError_t e, const char *what) -> int {
+        if (e == cudaSuccess) return SUNB_SUCCESS;
+        fail(ctx, SUNB_CUDA_ERROR, std::string("autotune: ") + what + ": " + cudaGetErrorString(e));
+        return restore(SUNB_CUDA_ERROR);
+    };
     for (int li = 0; li < 3; ++li) {
         if (configure_mech(ctx, Ls[li]) != SUNB_SUCCESS) { ctx->tune_ms[li][0] = -1.0f; continue; }
         const long long n = std::min<long long>(ctx->tune_cells, 8 * resident_cells(ctx));
-        CU(cudaMemcpyAsync(ctx->d_tune, ysrc, 8 * (size_t)n * ctx->N, cudaMemcpyDeviceToDevice, ctx->stream));
-        CU(cudaEventRecord(ev.a, ctx->stream));
-        int r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, n);
-        CU(cudaEventRecord(ev.b, ctx->stream));
-        CU(cudaEventSynchronize(ev.b));
-        if (r != SUNB_SUCCESS) {                 // back to the mapping it started from
-            const std::string why = ctx->err;
-            configure_mech(ctx, startL, startc);
-            ctx->err = why;
+        int r;
+        if ((r = cu(cudaMemcpyAsync(ctx->d_tune, ysrc, 8 * (size_t)n * ctx->N, cudaMemcpyDeviceToDevice,
+                                    ctx->stream), "copy")) != SUNB_SUCCESS)
             return r;
-        }
+        if ((r = cu(cudaEventRecord(ev.a, ctx->stream), "event")) != SUNB_SUCCESS) return r;
+        r = launch_mech(ctx, ctx->d_tune, t0, tout, nullptr, n);
+        if (r != SUNB_SUCCESS) return restore(r);
+        if ((r = cu(cudaEventRecord(ev.b, ctx->stream), "event")) != SUNB_SUCCESS) return r;
+        if ((r = cu(cudaEventSynchronize(ev.b), "trial")) != SUNB_SUCCESS) return r;
         float ms = 0.0f;
-        CU(cudaEventElapsedTime(&ms, ev.a, ev.b));
+        if ((r = cu(cudaEventElapsedTime(&ms, ev.a, ev.b), "timing")) != SUNB_SUCCESS) return r;
         ctx->tune_ms[li][0] = ms;
         ctx->tune_ms[li][1] = (float)n;
         const double per_cell = ms / (double)n;
@@ -1432,10 +1442,25 @@ int sunb_set_typical_tolerances(sunb_ctx *ctx, const double *dev_y, double rtol,
     return sunb_set_tolerances(ctx, rtol, 0.0, atol.data());
 }
 
-int sunb_set_params(sunb_ctx *ctx, const double *dev_params)
+// Bytes of the per-cell parameter array of a context (sunb_set_params).
+static size_t params_bytes(const sunb_ctx *ctx)
+{
+    switch (ctx->kind) {
+    case SUNB_ROBERTSON: return 8 * 3 * (size_t)ctx->C;
+    case SUNB_MECHANISM: return 8 * (size_t)ctx->C;
+    case SUNB_COSMOLOGY: return 8 * 2 * (size_t)ctx->C;
+    default: return 8 * (2 * (size_t)ctx->Cc + (size_t)ctx->C);
+    }
+}
+
+int sunb_set_params(sunb_ctx *ctx, const double *dev_params, size_t bytes)
 {
     if (!ctx) return SUNB_ILL_INPUT;
     if (!dev_params) return fail(ctx, SUNB_ILL_INPUT, "params is NULL");
+    const size_t want = params_bytes(ctx);
+    if (bytes != want)
+        return fail(ctx, SUNB_ILL_INPUT, "params: " + std::to_string(bytes) + " bytes given, the context's cells need " +
+                                             std::to_string(want));
     ctx->params = dev_params;
     return SUNB_SUCCESS;
 }
@@ -1457,7 +1482,7 @@ int sunb_integrate(sunb_ctx *ctx, double *dev_y, double t0, double tout, int32_t
     return launch_step(ctx, dev_y, t0, tout, dev_status);
 }
 
-int sunb_get_totals(sunb_ctx *ctx, sunb_totals *host_totals, int32_t *dev_cell_stats)
+int sunb_stats(sunb_ctx *ctx, sunb_stats_t *host_totals, int32_t *dev_cell_stats)
 {
     if (!ctx) return SUNB_ILL_INPUT;
     const long long n = ctx->C + ctx->Cc;
@@ -1510,7 +1535,7 @@ int sunb_integrate_host(sunb_ctx *ctx, double *host_y, double t0, double tout, i
     CU(cudaMemcpyAsync(host_y, ctx->d_ybuf, 8 * ny, cudaMemcpyDeviceToHost, ctx->stream));
     if (host_status)
         CU(cudaMemcpyAsync(host_status, ctx->d_sbuf, 4 * nc, cudaMemcpyDeviceToHost, ctx->stream));
-    return sunb_get_totals(ctx, nullptr, nullptr);
+    return sunb_stats(ctx, nullptr, nullptr);
 }
 
 int sunb_rhs(sunb_ctx *ctx, const double *dev_y, double *dev_f, int64_t n_cells)
@@ -1757,6 +1782,21 @@ int sunb_graph_launch(sunb_ctx *ctx, double t0)
     }
     CU(cudaGraphLaunch(ctx->graph_exec, ctx->stream));
     ctx->launches += (int64_t)ctx->graph_kernels.size();
+    return SUNB_SUCCESS;
+}
+
+int64_t sunb_tape_stride(const sunb_ctx *ctx) { return ctx && ctx->d_tape ? ctx->tape_stride : 0; }
+
+int sunb_get_tapes(sunb_ctx *ctx, int64_t first_cell, int64_t n_cells, double *host_out)
+{
+    if (!ctx) return SUNB_ILL_INPUT;
+    if (!ctx->d_tape) return fail(ctx, SUNB_NO_RECORD, "context created without record_adjoint");
+    if (first_cell < 0 || n_cells < 0 || first_cell + n_cells > ctx->C || (n_cells > 0 && !host_out))
+        return fail(ctx, SUNB_ILL_INPUT, "tapes: need 0 <= first_cell, first_cell + n_cells <= cells, host_out");
+    if (n_cells == 0) return SUNB_SUCCESS;
+    CU(cudaMemcpyAsync(host_out, ctx->d_tape + first_cell * ctx->tape_stride,
+                       8 * (size_t)n_cells * ctx->tape_stride, cudaMemcpyDeviceToHost, ctx->stream));
+    CU(cudaStreamSynchronize(ctx->stream));
     return SUNB_SUCCESS;
 }
 

@@ -24,10 +24,28 @@ def lib():
 
 
 def test_header_declares_the_boundary():
+    """The calls of the boundary: create / set_tolerances / set_params /
+    integrate / stats / adjoint / destroy / last_error, plus the single steps."""
     names = _declared()
     for n in ("sunb_create", "sunb_set_tolerances", "sunb_set_params", "sunb_integrate",
-              "sunb_get_totals", "sunb_rhs", "sunb_jac", "sunb_lu_solve_batched", "sunb_destroy"):
+              "sunb_stats", "sunb_adjoint", "sunb_destroy", "sunb_last_error", "sunb_rhs", "sunb_jac",
+              "sunb_lu_solve_batched", "sunb_get_tapes"):
         assert n in names
+
+
+def _signature(name):
+    txt = open(os.path.join(ROOT, "include", "sunb.h")).read()
+    txt = re.sub(r"/\*.*?\*/", "", txt, flags=re.S)
+    m = re.search(r"\b" + name + r"\s*\(([^)]*)\)", txt)
+    return [a.strip() for a in m.group(1).split(",")]
+
+
+def test_boundary_signatures():
+    """set_params carries the byte count of the parameter array, stats the
+    host totals and the optional per-cell device counters."""
+    assert _signature("sunb_set_params") == ["sunb_ctx *ctx", "const double *dev_params", "size_t bytes"]
+    assert _signature("sunb_stats") == ["sunb_ctx *ctx", "sunb_stats_t *host_totals", "int32_t *dev_per_cell"]
+    assert _signature("sunb_adjoint")[:3] == ["sunb_ctx *ctx", "const double *dev_dLdy", "double *dev_grad"]
 
 
 def test_library_exports_every_declared_symbol(lib):
@@ -50,6 +68,10 @@ def test_version_and_null_arguments_without_gpu(lib):
     assert lib.sunb_lu_solve_batched(0, 1, None, None, None, None, None) == sb.ILL_INPUT
     assert lib.sunb_lu_solve_batched(65, 1, None, None, None, None, None) == sb.ILL_INPUT
     assert lib.sunb_destroy(None) == 0
+    assert lib.sunb_set_params(None, None, 0) == sb.ILL_INPUT
+    assert lib.sunb_stats(None, None, None) == sb.ILL_INPUT
+    assert lib.sunb_get_tapes(None, 0, 0, None) == sb.ILL_INPUT
+    assert lib.sunb_tape_stride(None) == 0
 
 
 def test_library_is_built_for_sm_103a():
