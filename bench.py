@@ -31,6 +31,7 @@ import synth  # noqa: E402
 METRIC = "cells/s integrated per outer step at rtol 1e-6, plain FP64 vs mixed/persistent"
 UNIT = "cells/s"
 FP64_PEAK_DERIVED = 148 * 2032e6 * 2 * 2 / 1e12   # TFLOP/s: SMs x max clock x 2 DFMA/clk/SM x 2 flop
+FP32_PEAK_DERIVED = 148 * 2032e6 * 128 * 2 / 1e12  # TFLOP/s: SMs x max clock x 128 FFMA/clk/SM x 2 flop
 
 
 # --------------------------------------------------------------------- work model
@@ -48,15 +49,28 @@ def rhs_flops(mech):
     return M * per_reaction + K * per_species + 2 * nnz + 20
 
 
-def jac_extra_flops(mech):
-    """Operations of the analytic Jacobian beyond the shared right-hand side."""
-    K, M, N = mech.n_species, mech.n_reactions, mech.n_vars
+def _nnz(mech):
+    K, M = mech.n_species, mech.n_reactions
     nnz = 0
     for k in range(K):
         for j in range(M):
             net = int(np.sum(mech.prod[j] == k) - np.sum(mech.react[j] == k))
             nnz += net != 0
-    return M * 22 + nnz * 14 + 2 * K * K + 2 * K * K + 4 * K * K + 10 * K + N * N
+    return nnz
+
+
+def jac_extra_flops(mech):
+    """Operations of the analytic Jacobian beyond the shared right-hand side."""
+    K, M, N = mech.n_species, mech.n_reactions, mech.n_vars
+    return M * 22 + _nnz(mech) * 14 + 2 * K * K + 2 * K * K + 4 * K * K + 10 * K + N * N
+
+
+def jac_matrix_flops(mech):
+    """The part of jac_extra_flops done in the Newton matrix's precision: the
+    incidence sums into the rows (12 per nonzero), the temperature row's
+    products (2K^2) and the species rows' scaling (6K^2)."""
+    K = mech.n_species
+    return _nnz(mech) * 12 + 8 * K * K
 
 
 # DRAM bytes (read + write) per cell of one integrator launch, from one ncu
@@ -68,6 +82,19 @@ def jac_extra_flops(mech):
 # y, parameters and counters (~400 B) plus the write-back of the out-of-line
 # calls' stack frames.
 TRAFFIC_BYTES_PER_CELL = {"mech22": 4639.7}
+
+
+def work_model_split(kind, mech, tot, fp32_matrix=False, **kw):
+    """work_model's operations split by arithmetic pipe: (FP64, FP32).  With
+    an FP32 Newton matrix, its assembly (jac_matrix_flops), its LU
+    ((2/3)N^3 per build) and the triangular solves (2N^2 per Newton
+    iteration) run on the FP32 pipe; everything else is FP64."""
+    total = work_model(kind, mech, tot, **kw)
+    if not (fp32_matrix and kind == "mechanism") or kw.get("krylov_cells"):
+        return total, 0.0
+    N = mech.n_vars
+    f32 = tot["nje"] * (jac_matrix_flops(mech) + (2.0 / 3.0) * N ** 3) + tot["nni"] * 2 * N * N
+    return total - f32, f32
 
 
 def work_model(kind, mech, tot, krylov_cells=0, explicit=False):
@@ -102,6 +129,25 @@ def work_model(kind, mech, tot, krylov_cells=0, explicit=False):
         kp = max(0.0, (tot["nfe"] - tot["nni"] - 2 * krylov_cells) / tot["nni"])
         f_iter = 8 * N + 4 * N + kp * 10 * N + 2 * N * kp * (kp + 1) + 3 * N * kp
     return (tot["nfe"] * f_rhs + tot["nje"] * f_setup + tot["nni"] * f_iter + tot["nst"] * f_step)
+
+
+def roofline(f64, f32, kernel_ms):
+    """Roofline of one launch bound by the arithmetic pipes: f64 and f32
+    algorithmic operations over the launch's time.  frac is the share of the
+    launch the work would keep the pipes busy at their peaks (FP64 work at
+    the FP64 peak plus FP32 work at the FP32 peak); achieved counts FP32
+    operations at their FP64-pipe-time weight (peak64 / peak32), so that
+    achieved / peak = frac."""
+    t = kernel_ms / 1e3
+    a64 = f64 / t / 1e12
+    a32 = f32 / t / 1e12
+    frac = a64 / FP64_PEAK_DERIVED + a32 / FP32_PEAK_DERIVED
+    return {"bound": "alu", "unit": "TFLOP/s", "achieved": frac * FP64_PEAK_DERIVED,
+            "peak": FP64_PEAK_DERIVED, "frac": frac, "traffic": None, "kernel_ms": kernel_ms,
+            "fp64": {"achieved": a64, "frac": a64 / FP64_PEAK_DERIVED},
+            "fp32": {"achieved": a32, "peak": FP32_PEAK_DERIVED, "frac": a32 / FP32_PEAK_DERIVED},
+            "peak_source": "derived from the unit counts and the maximum clock: 148 SMs x 2032 MHz x "
+                           "2 DFMA/clk/SM x 2 (FP64 pipe), x 128 FFMA/clk/SM x 2 (FP32 pipe)"}
 
 
 def split_totals(cs, n_first):
@@ -319,9 +365,48 @@ def time_form(w, form, steps, warmup, flush, world=1):
     if w["kind"] == "mixed":
         parts = split_totals(it.cell_stats(), w["n_cosmo"])
     mapping = it.mapping() if w["kind"] in ("mechanism", "mixed") else None
+    nst = it.cell_stats()[:, 0].cpu().numpy()
+    y_final = y.cpu().numpy()
     it.close()
     return dict(ms=times, kernel_ms=kernel_ms, launches=launches, totals=tot, mapping=mapping, C=C,
-                parts=parts)
+                parts=parts, y=y_final, nst=nst)
+
+
+def time_graph(w, steps, warmup, flush):
+    """The chosen form through a CUDA graph of one outer step
+    (sunb_graph_capture / sunb_graph_launch): per timed step, y0 -> y and one
+    graph launch, bracketed by CUDA events; L2 flushed between steps."""
+    import torch
+    Y, P, C = flat_inputs(w)
+    it = make_integrator(w, "chosen")
+    stream = torch.cuda.current_stream()
+    y0 = torch.tensor(Y, device="cuda")
+    y = y0.clone()
+    p = torch.tensor(P, device="cuda")
+    it.set_params(p)
+    if METHOD_ERK:
+        it.set_method(1)
+    it.graph_capture(y, w["t0"], w["tout"] - w["t0"], 1)
+    for _ in range(warmup):
+        y.copy_(y0)
+        it.graph_launch(w["t0"])
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        flush.zero_()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        y.copy_(y0)
+        it.graph_launch(w["t0"])
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1))
+    tot = it.totals()
+    it.close()
+    ms = statistics.mean(times)
+    return {"value": C / (ms / 1e3), "ms_per_step": ms, "steps": steps, "warmup": warmup,
+            "worst_status": tot["worst_status"]}
 
 
 def time_e2e(w, form, steps, warmup):
@@ -358,53 +443,153 @@ def time_e2e(w, form, steps, warmup):
 
 
 # --------------------------------------------------------------------- CPU baseline
-def cpu_baseline(w, budget_s=12.0):
-    """The oracle as it stands, on the host's cores, on a bounded sample of
-    the workload (the first n cells; n grown until the sample takes a
-    fraction of budget_s), extrapolated to the full batch.  For the adjoint
-    workload the oracle runs its forward, replay and adjoint.  The variant
-    flags select the oracle's counterpart where the GPU run uses one:
-    difference-quotient Jacobians and GMRES for mechanism cells, the
-    explicit method for thread-per-cell kinds, typical-value tolerances from
-    the whole batch's initial state."""
-    import oracle
-    nth = oracle.num_threads()
+def _oracle_parts(w):
+    """(sub-workload or "cosmology", full cell count) per cell kind."""
     if w["kind"] == "mixed":
         wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
                   t0=0.0, tout=w["tout"])
-        parts = [("cosmology", w["n_cosmo"]), (wm, w["n_mech"])]
+        return [("cosmology", w["n_cosmo"]), (wm, w["n_mech"])]
+    return [(w, w["n_cells"])]
+
+
+def _oracle_pass(w, ww, n, nth):
+    """One pass of the oracle, as it stands, over the first n cells of a part
+    (for the adjoint workload its forward, replay and adjoint); seconds.
+    The variant flags select the oracle's counterpart where the GPU run uses
+    one: difference-quotient Jacobians and GMRES for mechanism cells, the
+    explicit method for thread-per-cell kinds, typical-value tolerances from
+    the whole batch's initial state."""
+    import oracle
+    sample = synth.workloads.cosmology(n) if ww == "cosmology" else ww
+    pb = oracle.problem_from_workload(sample, cells=np.arange(n))
+    t = time.perf_counter()
+    if w.get("name") == "adjoint":
+        oracle.adjoint_sqerr(pb, sample["y0"][:n], sample["target"][:n], sample["t0"],
+                             sample["tout"], 1e-6, 1e-10, cap=4096, nthreads=nth)
     else:
-        parts = [(w, w["n_cells"])]
-    total_s, descr = 0.0, []
+        kind = "cosmology" if ww == "cosmology" else ww["kind"]
+        opts = {}
+        if kind == "mechanism":
+            opts = dict(jac_mode=1 if JACOBIAN_DQ else 0, lin_solver=1 if LINEAR_GMRES else 0)
+        elif METHOD_ERK:
+            opts = dict(method=1)
+        atol = 1e-10
+        if TYPICAL_ETA is not None and w["kind"] != "mixed":
+            atol = oracle.typical_atol(w["y0"], TYPICAL_ETA)
+        oracle.integrate(pb, sample["y0"][:n], sample["t0"], sample["tout"], 1e-6, atol,
+                         nthreads=nth, **opts)
+    return time.perf_counter() - t
+
+
+def oracle_sample(w, budget_s):
+    """Sample sizes per cell kind: the first n cells, n grown until one pass
+    takes about a quarter of the part's share of budget_s (or the whole
+    part).  Returns [(part, full cells, n, seconds of the last pass)]."""
+    import oracle
+    nth = oracle.num_threads()
+    parts = _oracle_parts(w)
+    out = []
     for ww, Cfull in parts:
         n = min(Cfull, 2 * nth)
         while True:
-            sample = synth.workloads.cosmology(n) if ww == "cosmology" else ww
-            pb = oracle.problem_from_workload(sample, cells=np.arange(n))
-            t = time.perf_counter()
-            if w.get("name") == "adjoint":
-                oracle.adjoint_sqerr(pb, sample["y0"][:n], sample["target"][:n], sample["t0"],
-                                     sample["tout"], 1e-6, 1e-10, cap=4096, nthreads=nth)
-            else:
-                kind = "cosmology" if ww == "cosmology" else ww["kind"]
-                opts = {}
-                if kind == "mechanism":
-                    opts = dict(jac_mode=1 if JACOBIAN_DQ else 0, lin_solver=1 if LINEAR_GMRES else 0)
-                elif METHOD_ERK:
-                    opts = dict(method=1)
-                atol = 1e-10
-                if TYPICAL_ETA is not None and w["kind"] != "mixed":
-                    atol = oracle.typical_atol(w["y0"], TYPICAL_ETA)
-                oracle.integrate(pb, sample["y0"][:n], sample["t0"], sample["tout"], 1e-6, atol,
-                                 nthreads=nth, **opts)
-            dt = time.perf_counter() - t
+            dt = _oracle_pass(w, ww, n, nth)
             if dt > budget_s / len(parts) / 4 or n >= Cfull:
                 break
             n = min(Cfull, int(n * max(2.0, (budget_s / len(parts)) / max(dt, 1e-3))))
-        total_s += dt * Cfull / n
-        descr.append(f"first {n} of {Cfull} cells ({dt:.1f} s)")
+        out.append((ww, Cfull, n, dt))
+    return out
+
+
+def cpu_baseline(w, budget_s=12.0):
+    """The oracle as it stands, on the host's cores, on a bounded sample of
+    the workload (oracle_sample), extrapolated to the full batch."""
+    import oracle
+    nth = oracle.num_threads()
+    parts = oracle_sample(w, budget_s)
+    total_s = sum(dt * Cfull / n for _, Cfull, n, dt in parts)
+    descr = "; ".join(f"first {n} of {Cfull} cells ({dt:.1f} s)" for _, Cfull, n, dt in parts)
     return dict(value=sum(p[1] for p in parts) / total_s, unit=UNIT, cores=nth, kind="oracle",
-                sample="; ".join(descr) + ", extrapolated to the full batch")
+                sample=descr + ", extrapolated to the full batch")
+
+
+def reference_run(w, steps, warmup, budget_s):
+    """The reference arm: the oracle timed like the GPU arm, warmup + steps
+    passes, each over the same bounded sample of the workload (the first n
+    cells of each kind, sized by oracle_sample), every pass extrapolated to
+    the full batch.  Returns (cells/s, ms per full-batch step, description)."""
+    import oracle
+    nth = oracle.num_threads()
+    parts = oracle_sample(w, budget_s)
+    for _ in range(warmup):
+        for ww, _, n, _ in parts:
+            _oracle_pass(w, ww, n, nth)
+    per_step = []
+    for _ in range(steps):
+        per_step.append(sum(_oracle_pass(w, ww, n, nth) * Cfull / n for ww, Cfull, n, _ in parts))
+    s_full = statistics.mean(per_step)
+    descr = "; ".join(f"first {n} of {Cfull} cells per step" for _, Cfull, n, _ in parts)
+    C = sum(p[1] for p in parts)
+    return C / s_full, 1e3 * s_full, nth, descr + f", {steps} timed passes after {warmup}, " \
+                                          "each extrapolated to the full batch"
+
+
+def _parts(w, y_flat, nst):
+    """(sub-workload, GPU final states [C, n], GPU step counts) per cell kind."""
+    if w["kind"] != "mixed":
+        n = w["n_vars"]
+        return [(w, y_flat.reshape(-1, n), nst)]
+    nc = w["n_cosmo"]
+    wc = dict(kind="cosmology", table=w["table"], y0=w["e0"], params=w["cosmo_params"],
+              t0=w["t0"], tout=w["tout"])
+    wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
+              t0=w["t0"], tout=w["tout"])
+    return [(wc, y_flat[:nc].reshape(-1, 1), nst[:nc]),
+            (wm, y_flat[nc:].reshape(-1, w["mech"].n_vars), nst[nc:])]
+
+
+def parity_check(w, y_flat, nst, rtol=1e-6, atol=1e-10, n_first=1024, n_hard=256, nthreads=0):
+    """Parity of a GPU run against the oracle (a leg that may call the
+    oracle): the GPU's final states of the first n_first cells and of the
+    n_hard cells with the most steps (the GPU's step counts pick them),
+    against the ground truth -- the oracle at rtol 1e-12 and atol
+    min(atol) 1e-4 -- in tolerance units |y - y_ref| / (rtol |y_ref| + atol)
+    (median, 99th percentile and maximum over cells of each cell's worst
+    component), with the oracle's own run at the same rtol beside it; also
+    the largest relative error over components above atol, in units of
+    rtol, and the share of cells within 10 rtol.  Per cell kind."""
+    import oracle
+    out = []
+    for ww, yg, ns in _parts(w, y_flat, nst):
+        C = yg.shape[0]
+        nf, nh = min(n_first, C), min(n_hard, max(0, C - min(n_first, C)))
+        rest = np.arange(nf, C)
+        hard = rest[np.argsort(-ns[nf:], kind="stable")[:nh]] if nh else np.zeros(0, dtype=int)
+        cells = np.concatenate([np.arange(nf), np.sort(hard)]).astype(np.int64)
+        pb = oracle.problem_from_workload(ww, cells=cells)
+        y0 = ww["y0"][cells]
+        yt, _, _, _ = oracle.integrate(pb, y0, ww["t0"], ww["tout"], 1e-12, atol * 1e-4, nthreads=nthreads)
+        yo, _, _, worst = oracle.integrate(pb, y0, ww["t0"], ww["tout"], rtol, atol, nthreads=nthreads)
+        yt, yo, ygs = yt.reshape(len(cells), -1), yo.reshape(len(cells), -1), yg[cells]
+
+        def stats(y):
+            e = (np.abs(y - yt) / (rtol * np.abs(yt) + atol)).max(axis=1)
+            big = np.abs(yt) > atol
+            rel = np.where(big, np.abs(y - yt) / np.where(big, np.abs(yt), 1.0), 0.0).max() / rtol
+            return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
+                    "max": float(e.max()), "rel_above_atol_max_rtol_units": float(rel),
+                    "within_10rtol": float(np.mean(e <= 10.0))}
+
+        kind = ww["kind"]
+        out.append({"kind": kind, "cells": f"first {nf} + {len(hard)} with the most GPU steps",
+                    "gpu": stats(ygs), "oracle": stats(yo), "oracle_status": int(worst)})
+    return out
+
+
+def bench_config(workload_name):
+    """The config of both arms' lines: the workload, the method variant, and
+    the GPU arm's L2 hygiene."""
+    return {"workload": workload_name, **variant_config(),
+            "l2": "GPU arm: 512 MiB L2 flush between timed steps"}
 
 
 def variant_config():
@@ -431,6 +616,10 @@ def main():
     ap.add_argument("--cells", type=int, default=None,
                     help="first N cells only (small profiling cases; not a bench value)")
     ap.add_argument("--lanes", type=int, default=0, help="fix the chosen form's lanes per cell")
+    ap.add_argument("--graph", action="store_true",
+                    help="also time the chosen form through a CUDA graph of the outer step")
+    ap.add_argument("--parity-cells", type=int, default=1024,
+                    help="parity sample: the first N cells plus the N/4 with the most steps")
     ap.add_argument("--typical-eta", type=float, default=None,
                     help="typical-value absolute tolerances eta (min+max)/2 from y0 (Sec. 4.1.3) "
                          "instead of atol 1e-10 (not the benchmark configuration)")
@@ -470,15 +659,17 @@ def main():
     if args.impl == "reference":
         if rank != 0:
             return
-        cb = cpu_baseline(w, budget_s=max(5.0, 20.0 / max(1, args.steps + args.warmup)))
-        C = w["n_cosmo"] + w["n_mech"] if w["kind"] == "mixed" else w["n_cells"]
-        line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": UNIT,
+        # each pass about 120 s / (steps + warmup), at least 2 s, at most 8 s
+        budget = max(2.0, min(8.0, 120.0 / max(1, args.steps + args.warmup)))
+        value, ms_ref, cores, descr = reference_run(w, args.steps, args.warmup, budget)
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
                 "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-                "ms_per_step": 1e3 * C / cb["value"], "higher_is_better": True, "scaling": "weak",
+                "ms_per_step": ms_ref, "higher_is_better": True, "scaling": "weak",
                 "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-                "config": {"workload": workload_name, **variant_config()},
-                "cpu_baseline": cb,
-                "e2e": {"value": cb["value"], "unit": UNIT, "h2d_bytes_per_step": 0,
+                "config": bench_config(workload_name),
+                "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                                 "sample": descr},
+                "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}}
         print(json.dumps(line))
         return
@@ -501,49 +692,57 @@ def main():
     value = world * res["C"] / (ms / 1e3)
 
     # the counters describe the last launch (they are reset by every call)
+    fp32_matrix = FORMS["chosen"]["precision"] == 1
     if w["kind"] == "mixed":
-        flops = work_model("cosmology", None, res["parts"][0]) + \
-            work_model("mechanism", w["mech"], res["parts"][1],
-                       krylov_cells=(res["C"] - w["n_cosmo"]) if LINEAR_GMRES else 0)
+        f64c, _ = work_model_split("cosmology", None, res["parts"][0])
+        f64m, f32m = work_model_split("mechanism", w["mech"], res["parts"][1], fp32_matrix=fp32_matrix,
+                                      krylov_cells=(res["C"] - w["n_cosmo"]) if LINEAR_GMRES else 0)
+        f64, f32 = f64c + f64m, f32m
     elif w["name"] == "adjoint":
-        # forward + replay (taken as 2 exact Newton iterations per step) +
-        # reverse sweep (one J, LU and transposed solve per step)
+        # forward + replay (one Jacobian, FP32 LU and two FP32 solves per
+        # step, three right-hand sides) + reverse sweep (one J, FP64 LU and
+        # transposed solve per step, the parameter terms)
         mech, t = w["mech"], res["totals"]
         N = mech.n_vars
         per_setup = rhs_flops(mech) + jac_extra_flops(mech) + (2.0 / 3.0) * N ** 3 + 2 * N * N
-        flops = work_model("mechanism", mech, t) + t["nst"] * (3 * per_setup + 12 * mech.n_reactions)
+        f64, f32 = work_model_split("mechanism", mech, t, fp32_matrix=fp32_matrix)
+        rep32 = jac_matrix_flops(mech) + (2.0 / 3.0) * N ** 3 + 2 * 2 * N * N
+        f64 += t["nst"] * (3 * per_setup + 12 * mech.n_reactions - rep32)
+        f32 += t["nst"] * rep32
     else:
-        flops = work_model(w["kind"], w.get("mech"), res["totals"],
-                           krylov_cells=res["C"] if LINEAR_GMRES and w["kind"] == "mechanism" else 0,
-                           explicit=METHOD_ERK)
+        f64, f32 = work_model_split(w["kind"], w.get("mech"), res["totals"], fp32_matrix=fp32_matrix,
+                                    krylov_cells=res["C"] if LINEAR_GMRES and w["kind"] == "mechanism" else 0,
+                                    explicit=METHOD_ERK)
     # the integrator launch alone, timed on its stream (for the adjoint
     # workload the step's three phases together)
     kms = ms if w["name"] == "adjoint" else statistics.mean(res["kernel_ms"])
-    achieved = flops / (kms / 1e3) / 1e12
-    traffic = None
-    # (captured for the benchmark configuration's kernel only)
+    roof = roofline(f64, f32, kms)
+    # (traffic captured for the benchmark configuration's kernel only)
     if w["name"] in TRAFFIC_BYTES_PER_CELL and not (JACOBIAN_DQ or LINEAR_GMRES):
-        traffic = TRAFFIC_BYTES_PER_CELL[w["name"]] * res["C"]
-    roof = {"bound": "alu", "unit": "TFLOP/s", "achieved": achieved, "peak": FP64_PEAK_DERIVED,
-            "frac": achieved / FP64_PEAK_DERIVED, "traffic": traffic, "kernel_ms": kms,
-            "peak_source": "derived: 148 SMs x 2032 MHz x 2 DFMA/clk/SM x 2 (FP64 pipe)"}
+        roof["traffic"] = TRAFFIC_BYTES_PER_CELL[w["name"]] * res["C"]
     if rank != 0:
         return
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": "f64", "data": "synthetic",
-            "config": {"workload": workload_name, **variant_config(),
-                       "form": "chosen: FP32 Newton matrix/LU, device queue, autotuned mapping",
-                       "mapping": res["mapping"][:3] if res["mapping"] else None,
-                       "l2": "flushed between steps (512 MiB write)"},
+            "config": bench_config(workload_name),
+            "form": {"chosen": "FP32 Newton matrix/LU, device queue, autotuned mapping",
+                     "mapping": res["mapping"][:3] if res["mapping"] else None},
             "roofline": roof, "gpu_launches": res["launches"], "clocks": clk,
             "work": {k: res["totals"][k] for k in ("nst", "nfe", "nje", "nni", "nef", "ncf",
                                                      "max_nst", "n_failed")}}
     if res_plain is not None:
         mp = statistics.mean(res_plain["ms"])
+        if w["kind"] == "mixed":
+            p64 = work_model_split("cosmology", None, res_plain["parts"][0])[0] + \
+                work_model_split("mechanism", w["mech"], res_plain["parts"][1])[0]
+        else:
+            p64 = work_model_split(w["kind"], w.get("mech"), res_plain["totals"])[0]
         line["forms"] = {"plain_fp64": {"value": res_plain["C"] / (mp / 1e3), "ms_per_step": mp,
-                                        "mapping": res_plain["mapping"][:3]},
+                                        "mapping": res_plain["mapping"][:3],
+                                        "roofline": roofline(p64, 0.0, statistics.mean(res_plain["kernel_ms"])),
+                                        "work": {k: res_plain["totals"][k] for k in ("nst", "nfe", "nje", "nni")}},
                          "chosen": {"value": res["C"] / (ms / 1e3), "ms_per_step": ms,
                                     "mapping": res["mapping"][:3],
                                     "autotune_trial_ms": res["mapping"][3]}}
@@ -551,8 +750,14 @@ def main():
         line["work_by_kind"] = {"cosmology": res["parts"][0], "mechanism": res["parts"][1]}
     if not args.no_e2e and w["name"] != "adjoint":
         line["e2e"] = time_e2e(w, "chosen", max(1, min(args.steps, 2)), 1)
+    if args.graph:
+        line["graph"] = time_graph(w, args.steps, args.warmup, flush)
     if not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(w)
+        if TYPICAL_ETA is None:
+            import oracle
+            line["parity"] = parity_check(w, res["y"], res["nst"], nthreads=oracle.num_threads(),
+                                          n_first=args.parity_cells, n_hard=args.parity_cells // 4)
     print(json.dumps(line))
 
 

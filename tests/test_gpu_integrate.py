@@ -32,19 +32,23 @@ def _oracle_runs(w, cells=None):
     return ym, sm, yt
 
 
-def _assert_matches_method(yg, ym, yt, factor=3.0, floor=10.0):
+def _assert_matches_method(yg, ym, yt, factor=4.0):
     """The GPU's error distribution against the ground truth matches the
-    oracle's at the same rtol.  The synthetic mechanisms amplify local
-    errors up to ~1e3-fold, so two valid step sequences can differ by that
-    much on single cells: the median and the 90th percentile are held to
-    `factor`, the maximum (noisy on small samples) to 10x."""
+    oracle's at the same rtol, by ratios alone (no additive floors): the
+    median within `factor` (4), the 90th percentile within 3x and the
+    maximum within 5x.  Two valid step sequences decorrelate, so single
+    cells can differ by the synthetic mechanisms' ~1e3-fold amplification
+    of local errors; on B300 the ratios seen over every test of this suite
+    were at most 3.0 (median), 1.9 (p90) and 1.5 (maximum).  Element-by-
+    element parity on one step sequence is tested in test_gpu_frozen.py."""
     eg = tol_err(yg, yt, RTOL, ATOL)
     eo = tol_err(ym, yt, RTOL, ATOL)
     qg, qo = quantiles(eg), quantiles(eo)
     qg["p90"], qo["p90"] = float(np.quantile(eg, 0.9)), float(np.quantile(eo, 0.9))
-    assert qg["median"] <= factor * qo["median"] + 1.0, (qg, qo)
-    assert qg["p90"] <= factor * qo["p90"] + floor, (qg, qo)
-    assert qg["max"] <= 10.0 * qo["max"] + 10.0 * floor, (qg, qo)
+    print("distribution (GPU, oracle):", qg, qo)
+    assert qg["median"] <= factor * qo["median"], (qg, qo)
+    assert qg["p90"] <= 3.0 * qo["p90"], (qg, qo)
+    assert qg["max"] <= 5.0 * qo["max"], (qg, qo)
     return qg, qo
 
 
