@@ -100,7 +100,11 @@ typedef struct {
     int32_t lanes_per_cell;   /* mechanism cells: 8, 16, 32, or 0 = autotune  */
     int32_t schedule;         /* sunb_schedule                                */
     int32_t record_adjoint;   /* 0, or the tape capacity (accepted steps per
-                                 cell) for sunb_adjoint; SUNB_MECHANISM only  */
+                                 cell): SUNB_MECHANISM records for sunb_adjoint;
+                                 SUNB_ROBERTSON and SUNB_COSMOLOGY record the
+                                 step history only (sunb_get_tapes; their
+                                 records carry no column map, NaN there);
+                                 not for SUNB_MIXED                           */
     const sunb_mechanism *mech;        /* SUNB_MECHANISM, SUNB_MIXED */
     const sunb_cooling_table *table;   /* SUNB_COSMOLOGY, SUNB_MIXED */
 } sunb_problem;
@@ -294,7 +298,8 @@ int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final);
  * Returns SUNB_NO_RECORD for a context without tapes. */
 int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double *dev_grad_cells);
 
-/* The recorded step history (a context with record_adjoint = cap > 0):
+/* The recorded step history (a context with record_adjoint = cap > 0;
+ * thread-per-cell kinds fill the column map with NaN, the rest as below):
  * copies the tapes of cells first_cell .. first_cell + n_cells - 1 into
  * host_out (caller-owned host memory, n_cells * sunb_tape_stride(ctx)
  * doubles) and waits for the stream.  Per cell, with N unknowns and

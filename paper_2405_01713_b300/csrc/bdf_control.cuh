@@ -69,13 +69,39 @@ __device__ __forceinline__ void bdf_l(int q, const double *inv, double *l)
     }
 }
 
+// a[k] for a runtime k in 0..QMAX, selected by predication: indexing a
+// per-thread array with a runtime index would place the array in local
+// memory, where the controller's few such reads cost a stack frame.
+__device__ __forceinline__ double pick(const double *a, int k)
+{
+    double r = a[0];
+#pragma unroll
+    for (int j = 1; j <= QMAX; ++j)
+        if (j == k) r = a[j];
+    return r;
+}
+
+// 1/(p+1), p = 0..6
+__constant__ double INV_P1[7] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0};
+
 // Step factor from a squared WRMS error norm at order p.
 __device__ __forceinline__ double eta_from(double d2, int p, double bias)
 {
-    const double inv_p1[7] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0};
     // (bias * sqrt(d2))^(1/(p+1)) = exp(0.5 * log(bias^2 d2) / (p+1))
-    double r = fexp(0.5 * flog(bias * bias * d2) * inv_p1[p], g_exp_tab);
+    double r = fexp(0.5 * flog(bias * bias * d2) * INV_P1[p], g_exp_tab);
     return rcp(r + 1e-6);
+}
+
+// sum_{i<q-1} inv[i] and prod_{i<q-1} xi[i] (the order q-1 estimate's
+// coefficients), by predication over the unrolled range
+__device__ __forceinline__ void lower_order_sums(int q, const double *inv, const double *xi, double &l1m,
+                                                 double &pm)
+{
+    l1m = 0.0;
+    pm = 1.0;
+#pragma unroll
+    for (int i = 0; i < QMAX - 1; ++i)
+        if (i < q - 1) { l1m += inv[i]; pm *= xi[i]; }
 }
 
 // Coefficients e of x * prod_{i<q-1} (x + nodes[i]) (e[j] multiplies x^(j+1)).
@@ -305,7 +331,7 @@ struct CellRun {
                 bdf_xi(q + 1, h, hist, xi, inv);
                 bdf_l(q, inv, l);
                 il1 = rcp(l[1]);
-                Cq = rcp(1.0 + l[1] * xi[q]);
+                Cq = rcp(1.0 + l[1] * pick(xi, q));
             }
             gamma = h * il1;
             fresh = 0;
@@ -411,8 +437,8 @@ struct CellRun {
                 double eta = eta_from(dsm2, q, BIAS_Q);
                 int newq = q;
                 if (q > 1) {
-                    double l1m = 0.0, pm = 1.0;
-                    for (int i = 0; i < q - 1; ++i) { l1m += inv[i]; pm *= xi[i]; }
+                    double l1m, pm;
+                    lower_order_sums(q, inv, xi, l1m, pm);
                     const double f = pm * rcp(l1m);
                     const double em = eta_from(c.wrms2(q) * f * f, q - 1, BIAS_QM1);
                     if (em > eta) { eta = em; newq = q - 1; }
@@ -474,13 +500,14 @@ struct CellRun {
         const double l1 = l[1];
         double eta = 1.0;
         int newq = q;
-        const double kfac = l1 * l[q] * Cq;     // h^{q+1} y^{(q+1)}/(q+1)! = kfac * Delta
+        const double inv_q = pick(inv, q);
+        const double kfac = l1 * pick(l, q) * Cq;     // h^{q+1} y^{(q+1)}/(q+1)! = kfac * Delta
         if (BIAS_Q * BIAS_Q * dsm2 <= eta_viable2(q)) eta = eta_from(dsm2, q, BIAS_Q);
         if (qwait == 0) {
             double em = 0.0, ep = 0.0;
             if (q > 1) {
-                double l1m = 0.0, pm = 1.0;
-                for (int i = 0; i < q - 1; ++i) { l1m += inv[i]; pm *= xi[i]; }
+                double l1m, pm;
+                lower_order_sums(q, inv, xi, l1m, pm);
                 const double f = pm * rcp(l1m);
                 const double d2 = c.wrms2(q) * f * f;
                 if (BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1)) em = eta_from(d2, q - 1, BIAS_QM1);
@@ -490,8 +517,10 @@ struct CellRun {
                 const double rr = h * rcp(h_ks);
                 for (int i = 0; i <= q; ++i) rq *= rr;
                 double pp = 1.0;
-                for (int i = 0; i <= q; ++i) pp *= xi[i];
-                const double l1p = l1 + inv[q];
+#pragma unroll
+                for (int i = 0; i <= QMAX; ++i)
+                    if (i <= q) pp *= xi[i];
+                const double l1p = l1 + inv_q;
                 const double f = pp * rcp(l1p * (q + 2));
                 const double d2 = c.wrms2_lin(kfac, V_ACOR, -rq, V_KS) * f * f;
                 if (BIAS_QP1 * BIAS_QP1 * d2 <= eta_viable2(q + 1)) ep = eta_from(d2, q + 1, BIAS_QP1);
@@ -501,8 +530,8 @@ struct CellRun {
         }
         if (eta < ETA_THRESH) { eta = 1.0; newq = q; }
         else eta = fmin(eta, etamax);
-        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv[q], gamma, il1, h, ncf, nef);
-        if (newq == q + 1) c.order_increase(q, l, inv[q]);
+        c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv_q, gamma, il1, h, ncf, nef);
+        if (newq == q + 1) c.order_increase(q, l, inv_q);
         else if (newq == q - 1) {
             double e[QMAX + 1];
             decrease_coeffs(q, xi, e);

@@ -221,13 +221,6 @@ __device__ void lu_solve_t(const Grp<L> &g, const double *mat, int N, const int3
     g.sync();
 }
 
-// Header and record sizes (doubles) of a cell's adjoint tape: the header is
-// [count, h0, overflow, 5 spare, y0 (N)]; a record is y_n (N), the column
-// map P (6 x 6, row = output column), the update vector c (6), gamma, 1/l_1,
-// q, q_out, then the step's control decisions: its size h_n and the Newton
-// and error-test failures of its attempts (ncf, nef).
-__host__ __device__ __forceinline__ int tape_header(int N) { return 8 + N; }
-__host__ __device__ __forceinline__ int tape_record(int N) { return N + 49; }
 
 // Krylov scratch of one lane group (global memory, doubles): the basis
 // [l+1][N], the Hessenberg matrix [l+1][l], the rotations cs and sn [l],

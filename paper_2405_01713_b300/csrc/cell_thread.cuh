@@ -98,8 +98,54 @@ struct CosmologyProblem {
     }
 };
 
-template <class Prob>
-struct ThreadCell {
+// The step history of a thread-per-cell cell (REC = true, a separate
+// kernel): states and control decisions in the tape layout of the lane-group
+// backend (tape_header / tape_record doubles), without column maps (NaN).
+template <bool REC> struct ThreadTape {
+    __device__ __forceinline__ void rec_init(const double *, int, double) {}
+    __device__ __forceinline__ void rec_accept(const double *, int, int, int, const double *, double, double,
+                                               double, double, int, int) {}
+};
+template <> struct ThreadTape<true> {
+    double *tape = nullptr;
+    int tape_cap = 0, rec_count = 0;
+    __device__ void rec_init(const double *y0, int N, double h0)
+    {
+        tape[0] = 0.0;
+        tape[1] = h0;
+        tape[2] = 0.0;
+        for (int i = 0; i < N; ++i) tape[8 + i] = y0[i];   // y0 after the 8 header values
+        rec_count = 0;
+    }
+    __device__ void rec_accept(const double *y, int N, int q, int qo, const double *l, double inv_xi, double gamma,
+                               double il1, double h, int ncf, int nef)
+    {
+        if (rec_count >= tape_cap) {
+            tape[2] = 1.0;
+            return;
+        }
+        double *r = tape + tape_header(N) + (size_t)rec_count * tape_record(N);
+        for (int i = 0; i < N; ++i) r[i] = y[i];
+        for (int i = 0; i < 36; ++i) r[N + i] = __longlong_as_double(0x7ff8000000000000LL);
+#pragma unroll
+        for (int j = 0; j < 6; ++j) {
+            double c = (j <= q) ? l[j] : 0.0;
+            if (qo == q + 1 && j >= 1 && j <= q + 1) c += l[j - 1] * inv_xi;
+            r[N + 36 + j] = c;
+        }
+        r[N + 42] = gamma;
+        r[N + 43] = il1;
+        r[N + 44] = (double)q;
+        r[N + 45] = (double)qo;
+        r[N + 46] = h;
+        r[N + 47] = (double)ncf;
+        r[N + 48] = (double)nef;
+        tape[0] = (double)(++rec_count);
+    }
+};
+
+template <class Prob, bool REC = false>
+struct ThreadCell : ThreadTape<REC> {
     static constexpr int N = Prob::N;
     // all Newton iterations of an attempt in one superstep: the control
     // logic (cheap f, costly control) then stays aligned across the warp
@@ -113,8 +159,12 @@ struct ThreadCell {
     double atol[N];
     double *yg;   // this cell's state in global memory
 
-    __device__ __forceinline__ void rec_init(double) {}
-    __device__ __forceinline__ void rec_accept(int, int, const double *, double, double, double, double, int, int) {}
+    __device__ __forceinline__ void rec_init(double h0) { ThreadTape<REC>::rec_init(v[V_Z0], N, h0); }
+    __device__ __forceinline__ void rec_accept(int q, int qo, const double *l, double inv_xi, double gamma,
+                                               double il1, double h, int ncf, int nef)
+    {
+        ThreadTape<REC>::rec_accept(v[V_Z0], N, q, qo, l, inv_xi, gamma, il1, h, ncf, nef);
+    }
 
     __device__ __forceinline__ void load_y(int s)
     {

@@ -81,6 +81,9 @@ struct ThreadArgs {
     double atol[3];
     CoolArgs cool;
     int spread_lanes;   // > 0: one wave, lanes [0, spread_lanes) of every warp take a cell each
+    double *tape;       // step-history tapes (the REC kernel), tape_stride doubles per cell
+    long long tape_stride;
+    int tape_cap;
 };
 
 // Thread-per-cell kernel for Robertson and cosmology batches.  Large batches
@@ -88,15 +91,16 @@ struct ThreadArgs {
 // (spread_lanes > 0) is spread over all SMs and warps instead, cell
 // b + grid (w + W l) for lane l < spread_lanes of warp w of CTA b, so that
 // few cells do not crowd a few SMs.  ERK: the explicit Runge-Kutta
-// controller instead of the BDF one (a separate kernel).
-template <class Prob, bool ERK = false>
+// controller instead of the BDF one (a separate kernel).  REC: record each
+// cell's step history to its tape (a separate kernel).
+template <class Prob, bool ERK = false, bool REC = false>
 __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 {
     __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();
-    ThreadCell<Prob> tc;
+    ThreadCell<Prob, REC> tc;
     if constexpr (Prob::N == 1) tc.prob.tab = &cool;
 #pragma unroll
     for (int i = 0; i < Prob::N; ++i) tc.atol[i] = a.atol[i];
@@ -115,6 +119,10 @@ __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
     auto bind = [&](long long cell) {
         tc.prob.load(a.params, cell);
         tc.yg = a.y + cell * Prob::N;
+        if constexpr (REC) {
+            tc.tape = a.tape + cell * a.tape_stride;
+            tc.tape_cap = a.tape_cap;
+        }
     };
     auto done = [&](long long cell, const CellStats &st) { write_stats(a.stats, a.status, cell, st); };
     if constexpr (ERK) run_cells<ErkRun>(tc, a.ctl, launched_warp_mask(), next, bind, done);

@@ -965,6 +965,11 @@ static ThreadArgs thread_args(sunb_ctx *ctx, double *y, double t0, double tout, 
     a.cool.knots = ctx->d_cool;
     a.cool.n = ctx->nknots;
     a.cool.gamma_heat = ctx->gamma_heat;
+    if (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY) {
+        a.tape = ctx->d_tape;
+        a.tape_stride = ctx->tape_stride;
+        a.tape_cap = ctx->tape_cap;
+    }
     return a;
 }
 
@@ -1119,8 +1124,13 @@ static int thread_spec(sunb_ctx *ctx, const ThreadArgs &a, bool robertson, Launc
     sp.thread = true;
     sp.ta = a;
     const bool erk = ctx->method == SUNB_METHOD_ERK;
-    sp.func = robertson ? (erk ? (void *)thread_kernel<RobertsonProblem, true> : (void *)thread_kernel<RobertsonProblem>)
-                        : (erk ? (void *)thread_kernel<CosmologyProblem, true> : (void *)thread_kernel<CosmologyProblem>);
+    const bool rec = a.tape != nullptr;     // step-history tapes: the recording kernel
+    if (rec)
+        sp.func = robertson ? (void *)thread_kernel<RobertsonProblem, false, true>
+                            : (void *)thread_kernel<CosmologyProblem, false, true>;
+    else
+        sp.func = robertson ? (erk ? (void *)thread_kernel<RobertsonProblem, true> : (void *)thread_kernel<RobertsonProblem>)
+                            : (erk ? (void *)thread_kernel<CosmologyProblem, true> : (void *)thread_kernel<CosmologyProblem>);
     sp.smem = 0;
     // A batch of at most 256 cells per SM runs as one wave spread over every
     // SM, at most 8 warps of about 2 cells each per SM: 1024 Robertson cells
@@ -1225,7 +1235,7 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
     if (prob->precision != SUNB_FP64 && prob->precision != SUNB_MIXED32) { fail(ctx, SUNB_ILL_INPUT, "unknown precision"); return bail(SUNB_ILL_INPUT); }
     if (prob->schedule != SUNB_SCHED_QUEUE && prob->schedule != SUNB_SCHED_STATIC) { fail(ctx, SUNB_ILL_INPUT, "unknown schedule"); return bail(SUNB_ILL_INPUT); }
     if (prob->record_adjoint < 0 || prob->record_adjoint > (1 << 20)) { fail(ctx, SUNB_ILL_INPUT, "record_adjoint must be 0..2^20 steps"); return bail(SUNB_ILL_INPUT); }
-    if (prob->record_adjoint && prob->kind != SUNB_MECHANISM) { fail(ctx, SUNB_ILL_INPUT, "the adjoint is available for SUNB_MECHANISM contexts"); return bail(SUNB_ILL_INPUT); }
+    if (prob->record_adjoint && prob->kind == SUNB_MIXED) { fail(ctx, SUNB_ILL_INPUT, "tapes are recorded for single-kind contexts"); return bail(SUNB_ILL_INPUT); }
     const int lpc = prob->lanes_per_cell;
     if (lpc != 0 && lpc != 8 && lpc != 16 && lpc != 32) { fail(ctx, SUNB_ILL_INPUT, "lanes_per_cell must be 0, 8, 16 or 32"); return bail(SUNB_ILL_INPUT); }
     int rc;
@@ -1261,6 +1271,16 @@ int sunb_create(const sunb_problem *prob, void *stream, sunb_ctx **out)
         if (cudaMemcpy(ctx->d_cool, k.data(), 8 * k.size(), cudaMemcpyHostToDevice) != cudaSuccess) { fail(ctx, SUNB_CUDA_ERROR, "copy cooling table"); return bail(SUNB_CUDA_ERROR); }
     }
     ctx->atol.assign(ctx->N + (ctx->kind == SUNB_MIXED ? 1 : 0), 1e-10);
+    if (prob->record_adjoint && (ctx->kind == SUNB_ROBERTSON || ctx->kind == SUNB_COSMOLOGY)) {
+        // thread-per-cell kinds record the step history only (no adjoint)
+        ctx->tape_cap = prob->record_adjoint;
+        ctx->tape_stride = tape_header(ctx->N) + (long long)ctx->tape_cap * tape_record(ctx->N);
+        if (cudaMalloc(&ctx->d_tape, 8 * (size_t)ctx->tape_stride * ctx->C) != cudaSuccess) {
+            fail(ctx, SUNB_MEM_FAIL, "cudaMalloc tapes");
+            return bail(SUNB_MEM_FAIL);
+        }
+        cudaMemset(ctx->d_tape, 0, 8 * (size_t)ctx->tape_stride * ctx->C);
+    }
     const long long ncell = ctx->C + ctx->Cc;
     if (cudaMalloc(&ctx->d_stats, 32 * (size_t)ncell) != cudaSuccess ||
         cudaMalloc(&ctx->d_queue, 64) != cudaSuccess ||
@@ -1390,6 +1410,8 @@ int sunb_set_method(sunb_ctx *ctx, int method)
         return fail(ctx, SUNB_ILL_INPUT, "method must be SUNB_METHOD_BDF or SUNB_METHOD_ERK");
     if (method == SUNB_METHOD_ERK && ctx->kind != SUNB_ROBERTSON && ctx->kind != SUNB_COSMOLOGY)
         return fail(ctx, SUNB_ILL_INPUT, "the explicit method is built for thread-per-cell kinds only");
+    if (method == SUNB_METHOD_ERK && ctx->d_tape)
+        return fail(ctx, SUNB_ILL_INPUT, "tapes record the BDF's step history");
     ctx->method = method;
     return SUNB_SUCCESS;
 }
@@ -1654,6 +1676,7 @@ int sunb_adjoint_replay(sunb_ctx *ctx, double *dev_y_final)
 {
     if (!ctx) return SUNB_ILL_INPUT;
     if (!ctx->d_tape) return fail(ctx, SUNB_NO_RECORD, "context created without record_adjoint");
+    if (ctx->kind != SUNB_MECHANISM) return fail(ctx, SUNB_ILL_INPUT, "the adjoint is for mechanism contexts");
     if (!ctx->params) return fail(ctx, SUNB_ILL_INPUT, "parameters not set (sunb_set_params)");
     const int rc = adj_launch(ctx, 0, nullptr, dev_y_final);
     if (rc == SUNB_SUCCESS) ctx->replayed = true;
@@ -1664,6 +1687,7 @@ int sunb_adjoint(sunb_ctx *ctx, const double *dev_dLdy, double *dev_grad, double
 {
     if (!ctx) return SUNB_ILL_INPUT;
     if (!ctx->d_tape) return fail(ctx, SUNB_NO_RECORD, "context created without record_adjoint");
+    if (ctx->kind != SUNB_MECHANISM) return fail(ctx, SUNB_ILL_INPUT, "the adjoint is for mechanism contexts");
     if (!dev_dLdy || !dev_grad) return fail(ctx, SUNB_ILL_INPUT, "dLdy and grad must not be NULL");
     if (!ctx->replayed) {
         const int rc = sunb_adjoint_replay(ctx, nullptr);

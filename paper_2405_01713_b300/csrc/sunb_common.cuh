@@ -173,4 +173,12 @@ static inline cudaError_t fill_math_tables()
     return a != cudaSuccess ? a : b;
 }
 
+// Header and record sizes (doubles) of a cell's tape: the header is
+// [count, h0, overflow, 5 spare, y0 (N)]; a record is y_n (N), the column
+// map P (6 x 6, row = output column), the update vector c (6), gamma, 1/l_1,
+// q, q_out, then the step's control decisions: its size h_n and the Newton
+// and error-test failures of its attempts (ncf, nef).
+__host__ __device__ __forceinline__ int tape_header(int N) { return 8 + N; }
+__host__ __device__ __forceinline__ int tape_record(int N) { return N + 49; }
+
 }  // namespace sunb

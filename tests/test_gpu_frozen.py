@@ -12,15 +12,16 @@ Newton iteration, not in the equations solved).  Gradients: 1e-8 of the
 cell's largest gradient component of each kind (ln A, Ea).  Coefficients:
 1e-13 relative.  Decisions: the error test passes on every accepted step
 (to rounding), and the step factor and order the oracle chooses from the
-GPU's corrections equal the recorded ones (step factors to 1e-6: both
-sides' corrections differ at the 1e-10 level relative, since they are
-differences of nearly equal states).
+GPU's corrections equal the recorded ones (step factors to 1e-5: both
+sides' corrections differ at the 1e-10 level relative or more, since they
+are differences of nearly equal states, and the factor is a power of their
+norm; the worst seen on B300 was 9e-7).
 """
 import numpy as np
 import pytest
 
 import synth
-from frozen_util import check_frozen, gpu_tapes, summarise
+from frozen_util import check_follow, check_frozen, gpu_tapes, summarise, summarise_follow
 from gpu_util import need_gpu, sb, torch
 
 pytestmark = pytest.mark.gpu
@@ -61,3 +62,50 @@ def test_mech54_frozen_sequence(precision):
     s = summarise(check_frozen(w, g))
     print("mech54", precision, s)
     _assert_frozen(s, precision)
+
+
+@pytest.mark.parametrize("kind", ["cosmology", "robertson"])
+def test_thread_per_cell_kinds_follow_their_decisions(kind):
+    """Cosmology (the heating-cooling cells of the mixed batch) and Robertson
+    cells record their step history through the recording thread kernel;
+    the oracle re-takes every recorded decision from the recorded states,
+    and the coefficients the GPU used equal its own."""
+    need_gpu()
+    m = sb()
+    if kind == "cosmology":
+        w = synth.workloads.cosmology(512)
+        it = m.Integrator(m.COSMOLOGY, 512, table=w["table"], record_adjoint=2048)
+    else:
+        w = synth.workloads.robertson(64)
+        it = m.Integrator(m.ROBERTSON, 64, record_adjoint=2048)
+    it.set_tolerances(w["rtol"], w["atol"])
+    it.set_params(torch.tensor(w["params"], device="cuda"))
+    y = torch.tensor(w["y0"], device="cuda")
+    it.integrate(y, w["t0"], w["tout"])
+    assert it.totals()["worst_status"] == 0
+    tapes = it.tapes()
+    assert np.allclose([t["y"][-1] for t in tapes], y.cpu().numpy(), rtol=0, atol=0)
+    s = summarise_follow(check_follow(w, tapes))
+    print(kind, s)
+    assert s["gamma"] < 1e-13 and s["il1"] < 1e-13 and s["c"] < 1e-13, s
+    assert s["dsm_max"] < 1.0 + 1e-8, s
+    assert s["eta_agree"] == 1.0 and s["order_agree"] == 1.0, s
+    assert s["eta_compared"] > 0.5 * s["steps"] and s["order_choices"] > 0, s
+    assert s["newton_err_p99"] < 0.1, s
+
+
+def test_recording_kernel_gives_the_same_bytes():
+    """Recording takes the same arithmetic: the recording thread kernel's
+    states equal the plain kernel's bit for bit."""
+    need_gpu()
+    m = sb()
+    w = synth.workloads.cosmology(4096)
+    out = []
+    for cap in (0, 2048):
+        it = m.Integrator(m.COSMOLOGY, 4096, table=w["table"], record_adjoint=cap)
+        it.set_tolerances(w["rtol"], w["atol"])
+        it.set_params(torch.tensor(w["params"], device="cuda"))
+        y = torch.tensor(w["y0"], device="cuda")
+        it.integrate(y, w["t0"], w["tout"])
+        out.append(y.cpu().numpy())
+    np.testing.assert_array_equal(out[0], out[1])
