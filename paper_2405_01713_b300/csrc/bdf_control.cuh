@@ -138,14 +138,17 @@ __constant__ double GEAR_IL1[QMAX + 1] = {1.0, 1.0, 2.0 / 3.0, 6.0 / 11.0, 12.0 
 __constant__ double GEAR_CQ[QMAX + 1] = {1.0, 1.0 / 3.0, 2.0 / 11.0, 6.0 / 50.0, 12.0 / 137.0, 60.0 / 882.0};
 
 // eta_p >= 1.5 exactly when bias^2 * ||E_p||^2 <= (2/3 - 1e-6)^(2(p+1)):
-// the step-size choice takes the power only when a change can follow.
-__device__ __forceinline__ double eta_viable2(int p)
+// the step-size choice takes the power only when a change can follow.  The
+// thresholds for p = 0..6, evaluated by the compiler.
+constexpr double viable2_value(int p)
 {
-    const double b = 2.0 / 3.0 - 1e-6;
     double r = 1.0;
-    for (int i = 0; i < 2 * (p + 1); ++i) r *= b;
+    for (int i = 0; i < 2 * (p + 1); ++i) r *= 2.0 / 3.0 - 1e-6;
     return r;
 }
+__constant__ double ETA_VIABLE2[7] = {viable2_value(0), viable2_value(1), viable2_value(2), viable2_value(3),
+                                      viable2_value(4), viable2_value(5), viable2_value(6)};
+__device__ __forceinline__ double eta_viable2(int p) { return ETA_VIABLE2[p]; }
 
 // The first steps of a cell for the explicit controller, the same as
 // CellRun::begin_body's: y0 into V_Z0, f(t0, y0) into V_F, the weights from

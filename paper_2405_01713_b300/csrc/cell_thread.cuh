@@ -42,6 +42,7 @@ struct CoolingSmem {
     double gamma_heat;
     const double *lnT, *lnLam, *slope;
     const double *exptab;      // 2^(j/64), for fexp
+    const float *lnTf;         // lnT rounded to float, for the knot search
 };
 
 // Heating-cooling of one gas cell (the Nyx split equation of Sec. 3.2,
@@ -63,17 +64,25 @@ struct CosmologyProblem {
         const double lnT = flog(T);
         const double *x = tab->lnT;
         const int n = tab->n;
+        // segment lo = the last knot i <= n - 2 with x[i] <= lnT (0 below
+        // the first knot): a binary search on the float copy of the knots
+        // (the FP32 pipe), then exact FP64 comparisons that move lo across
+        // any knot the rounding to float put on the wrong side of lnT
+        const float *xf = tab->lnTf;
+        const float lf = (float)lnT;
         int lo;
-        if (lnT <= x[0]) lo = 0;
-        else if (lnT >= x[n - 1]) lo = n - 2;
+        if (lf <= xf[0]) lo = 0;
+        else if (lf >= xf[n - 1]) lo = n - 2;
         else {
             lo = 0;
             int hi = n - 1;
             while (hi - lo > 1) {
                 const int mid = (lo + hi) >> 1;
-                if (x[mid] <= lnT) lo = mid; else hi = mid;
+                if (xf[mid] <= lf) lo = mid; else hi = mid;
             }
         }
+        while (lo > 0 && !(x[lo] <= lnT)) --lo;
+        while (lo < n - 2 && x[lo + 1] <= lnT) ++lo;
         const double sl = tab->slope[lo];
         const double lam = fexp(tab->lnLam[lo] + sl * (lnT - x[lo]), tab->exptab);
         const double heat = tab->gamma_heat * fexp(-0.7 * (lnT - LN1E4), tab->exptab);

@@ -57,10 +57,19 @@ __device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned c
     for (int i = threadIdx.x; i < bytes / 16; i += blockDim.x) d[i] = s[i];
 }
 
+// The cooling table in shared memory: lnT, lnLam, slope (n each, the last
+// slope unused), the exp table, then lnT rounded to float (the knot search).
+__host__ __device__ __forceinline__ int cooling_smem_bytes(int n)
+{
+    return 8 * (3 * n + EXP_TABLE_SIZE) + 4 * n;
+}
+
 __device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const CoolArgs &c)
 {
     double *d = reinterpret_cast<double *>(dst);
+    float *df = reinterpret_cast<float *>(d + 3 * c.n + EXP_TABLE_SIZE);
     for (int i = threadIdx.x; i < 3 * c.n + EXP_TABLE_SIZE; i += blockDim.x) d[i] = c.knots[i];
+    for (int i = threadIdx.x; i < c.n; i += blockDim.x) df[i] = (float)c.knots[i];
     CoolingSmem t;
     t.n = c.n;
     t.gamma_heat = c.gamma_heat;
@@ -68,6 +77,7 @@ __device__ __forceinline__ CoolingSmem stage_cooling(unsigned char *dst, const C
     t.lnLam = d + c.n;
     t.slope = d + 2 * c.n;
     t.exptab = d + 3 * c.n;
+    t.lnTf = df;
     return t;
 }
 
@@ -96,7 +106,7 @@ struct ThreadArgs {
 template <class Prob, bool ERK = false, bool REC = false>
 __global__ void __launch_bounds__(256) thread_kernel(const ThreadArgs a)
 {
-    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
+    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE + 128];
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();

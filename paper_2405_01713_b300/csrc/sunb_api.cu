@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(128) mech_eval_kernel(const MechArgs a, const 
 template <class Prob>
 __global__ void thread_eval_kernel(const ThreadArgs a, const double *y, double *out, long long n, int mode)
 {
-    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE];
+    __shared__ __align__(16) double cool_s[3 * 256 + EXP_TABLE_SIZE + 128];
     CoolingSmem cool;
     if (Prob::N == 1) cool = stage_cooling(reinterpret_cast<unsigned char *>(cool_s), a.cool);
     __syncthreads();
@@ -786,7 +786,7 @@ static void *pick_mech_kernel(int L, int precision, bool cosmo, bool krylov)
     return nullptr;
 }
 
-static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(8 * (3 * c->nknots + EXP_TABLE_SIZE)) : 0; }
+static int cool_bytes(const sunb_ctx *c) { return c->nknots ? align16(cooling_smem_bytes(c->nknots)) : 0; }
 
 // Shared memory of a mechanism CTA with c cells of L lanes: the tables, the
 // cooling table (mixed launches), the cells, one Newton-matrix scratch per

@@ -99,6 +99,30 @@ def test_robertson_and_cosmology_rhs_jac():
         np.testing.assert_allclose(J[c], Jo, rtol=1e-12, atol=1e-300)
 
 
+def test_cosmology_rhs_next_to_every_knot():
+    """The cooling law's segment is found by a search on float copies of the
+    knots, then exact FP64 comparisons: temperatures within float rounding of
+    every knot (ln T within 1e-9 .. 1e-6 of it, on both sides) take the
+    oracle's segment -- f and df/de (whose slope tells the segment) agree."""
+    need_gpu()
+    m = sb()
+    w = synth.workloads.cosmology(1)
+    lnT = np.asarray(w["table"].lnT)
+    d = np.array([-1e-6, -1e-7, -1e-9, 1e-9, 1e-7, 1e-6])
+    e = np.exp(lnT[:, None] + d[None, :]).reshape(-1, 1)
+    C = e.shape[0]
+    P = np.tile(w["params"][:1], (C, 1))
+    it = m.Integrator(m.COSMOLOGY, C, table=w["table"])
+    it.set_params(dev(P))
+    f = it.rhs(dev(e)).cpu().numpy()
+    J = it.jac(dev(e)).cpu().numpy()
+    wc = dict(w, params=P)
+    pb = oracle.problem_from_workload(wc)
+    for c in range(C):
+        np.testing.assert_allclose(f[c], oracle.rhs(pb, e[c], c), rtol=1e-12, atol=1e-300)
+        np.testing.assert_allclose(J[c], oracle.jac(pb, e[c], c), rtol=1e-12, atol=1e-300)
+
+
 @pytest.mark.parametrize("n", [1, 3, 22, 33, 54, 64])
 def test_batched_lu_matches_oracle(n):
     """Pivot sequences bit-exact; factors and solutions to rounding."""
