@@ -547,7 +547,8 @@ def _parts(w, y_flat, nst):
             (wm, y_flat[nc:].reshape(-1, w["mech"].n_vars), nst[nc:])]
 
 
-def parity_check(w, y_flat, nst, rtol=1e-6, atol=1e-10, n_first=1024, n_hard=256, nthreads=0):
+def parity_check(w, y_flat, nst, rtol=1e-6, atol=1e-10, n_first=1024, n_hard=256, nthreads=0,
+                 per_cell=None):
     """Parity of a GPU run against the oracle (a leg that may call the
     oracle): the GPU's final states of the first n_first cells and of the
     n_hard cells with the most steps (the GPU's step counts pick them),
@@ -556,7 +557,9 @@ def parity_check(w, y_flat, nst, rtol=1e-6, atol=1e-10, n_first=1024, n_hard=256
     (median, 99th percentile and maximum over cells of each cell's worst
     component), with the oracle's own run at the same rtol beside it; also
     the largest relative error over components above atol, in units of
-    rtol, and the share of cells within 10 rtol.  Per cell kind."""
+    rtol, and the share of cells within 10 rtol; for the cells beyond that
+    bar, how the oracle's own run fares on them.  Per cell kind; per_cell
+    (a list, optional) receives the cells and both runs' errors."""
     import oracle
     out = []
     for ww, yg, ns in _parts(w, y_flat, nst):
@@ -571,17 +574,32 @@ def parity_check(w, y_flat, nst, rtol=1e-6, atol=1e-10, n_first=1024, n_hard=256
         yo, _, _, worst = oracle.integrate(pb, y0, ww["t0"], ww["tout"], rtol, atol, nthreads=nthreads)
         yt, yo, ygs = yt.reshape(len(cells), -1), yo.reshape(len(cells), -1), yg[cells]
 
+        def cell_err(y):
+            return (np.abs(y - yt) / (rtol * np.abs(yt) + atol)).max(axis=1)
+
         def stats(y):
-            e = (np.abs(y - yt) / (rtol * np.abs(yt) + atol)).max(axis=1)
+            e = cell_err(y)
             big = np.abs(yt) > atol
             rel = np.where(big, np.abs(y - yt) / np.where(big, np.abs(yt), 1.0), 0.0).max() / rtol
             return {"median": float(np.median(e)), "p99": float(np.quantile(e, 0.99)),
                     "max": float(e.max()), "rel_above_atol_max_rtol_units": float(rel),
                     "within_10rtol": float(np.mean(e <= 10.0))}
 
+        eg, eo = cell_err(ygs), cell_err(yo)
+        beyond = eg > 10.0
+        # the cells beyond the 10 rtol bar, seen by the oracle's own run at
+        # the same rtol: the share that the oracle also misses the bar on,
+        # and the median ratio of the two errors there
+        expl = {"cells": int(beyond.sum()),
+                "oracle_also_beyond": float(np.mean(eo[beyond] > 10.0)) if beyond.any() else None,
+                "median_gpu_over_oracle": float(np.median(eg[beyond] / np.maximum(eo[beyond], 1e-300)))
+                if beyond.any() else None}
         kind = ww["kind"]
         out.append({"kind": kind, "cells": f"first {nf} + {len(hard)} with the most GPU steps",
-                    "gpu": stats(ygs), "oracle": stats(yo), "oracle_status": int(worst)})
+                    "gpu": stats(ygs), "oracle": stats(yo), "oracle_status": int(worst),
+                    "beyond_10rtol": expl})
+        if per_cell is not None:
+            per_cell.append({"kind": kind, "cells": cells, "gpu": eg, "oracle": eo})
     return out
 
 
