@@ -291,7 +291,8 @@ struct CellRun {
         c.newton_init();
         delp2 = 0.0;
         R2 = 1.0;
-        cstale = (gamma != gamma_M) ? 2.0 * rcp(1.0 + gamma * rcp(gamma_M)) : 1.0;
+        // 2/(1 + gamma/gamma_M) with one reciprocal
+        cstale = (gamma != gamma_M) ? 2.0 * gamma_M * rcp(gamma_M + gamma) : 1.0;
         m = 0;
         phase = PH_NEWTON;
     }
@@ -344,7 +345,7 @@ struct CellRun {
                 start_newton(c);
             } else {
                 if (force_setup || !have_M || s.nst >= nst_lastsetup + MSBP ||
-                    fabs(gamma * rcp(gamma_M) - 1.0) > DGMAX)
+                    fabs(gamma - gamma_M) > DGMAX * gamma_M)        // |gamma/gamma_M - 1| > DGMAX
                     phase = PH_SETUP;
                 else
                     start_newton(c);

@@ -113,3 +113,46 @@ def test_adjoint_full_batch():
     rel = np.linalg.norm((gc[cells] - go).reshape(len(cells), -1), axis=1) / \
         np.linalg.norm(go.reshape(len(cells), -1), axis=1)
     assert np.median(rel) < 1e-3, rel
+    # the same sampled cells on the GPU's own step sequences: the oracle's
+    # exact replay and adjoint of the map rebuilt from the recorded decisions
+    yrep, dLn = yrep.cpu().numpy(), dL.cpu().numpy()
+    for i, c in enumerate(cells):
+        t = it.tapes(int(c), 1)[0]
+        td = oracle.Tape.from_decisions(t["y0"], t["h0"], t["h"], t["q"], t["qo"], t["ncf"], t["nef"])
+        yf, ys = oracle.replay_tape_states(pb, td, i)
+        assert np.max(np.abs(t["y"] - ys) / (np.abs(ys) + ATOL)) < 1e-10      # exact states per step
+        assert np.max(np.abs(yrep[c] - yf) / (np.abs(yf) + ATOL)) < 1e-10
+        g1 = oracle.adjoint_tape(pb, td, dLn[c], i)
+        assert np.max(np.abs(gc[c] - g1).max(axis=0) / np.abs(g1).max(axis=0)) < 1e-8
+
+
+def test_mech22_frozen_sequence_at_scale():
+    """2^14 mech22 cells with tapes in the benchmarked form (FP32 Newton
+    matrix, queue, autotuned mapping): 24 sampled cells compared element
+    by element on their own step sequences (see test_gpu_frozen)."""
+    need_gpu()
+    from frozen_util import check_frozen, summarise
+    m = sb()
+    w = synth.workloads.mech22(2 ** 14)
+    C = w["n_cells"]
+    it = m.Integrator(m.MECHANISM, C, mech=w["mech"], record_adjoint=2048, precision=1, lanes_per_cell=0)
+    it.set_tolerances(RTOL, ATOL)
+    it.set_params(dev(w["params"]))
+    y = dev(w["y0"])
+    it.integrate(y, w["t0"], w["tout"])
+    assert it.totals()["worst_status"] == 0
+    cells = _sample(C, 24, seed=22)
+    fwd = [it.tapes(int(c), 1)[0] for c in cells]
+    yrep = it.adjoint_replay().cpu().numpy()
+    exact = [it.tapes(int(c), 1)[0] for c in cells]
+    K = w["mech"].n_species
+    dL = np.zeros((len(cells), w["mech"].n_vars))
+    dL[:, :K] = 2.0 * (yrep[cells, :K] - 0.05)
+    dLfull = torch.zeros((C, w["mech"].n_vars), dtype=torch.float64, device="cuda")
+    dLfull[torch.tensor(cells, device="cuda")] = dev(dL)
+    _, gc = it.adjoint(dLfull, per_cell=True)
+    g = dict(fwd=fwd, exact=exact, yrep=yrep[cells], dL=dL, grad_cells=gc.cpu().numpy()[cells])
+    s = summarise(check_frozen(w, g, cells=cells))
+    print("mech22 2^14 chosen", it.mapping()[:3], s)
+    assert s["states"] < 1e-10 and s["final"] < 1e-10 and s["grad"] < 1e-8, s
+    assert s["dsm_max"] < 1.0 + 1e-8 and s["eta_agree"] == 1.0 and s["order_agree"] == 1.0, s

