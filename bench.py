@@ -74,14 +74,18 @@ def jac_matrix_flops(mech):
 
 
 # DRAM bytes (read + write) per cell of one integrator launch, from one ncu
-# capture of a smaller batch of the same kernel and launch shape, scaled by
-# cells (traffic is per cell: y in and out, parameters, counters):
-#   ncu --set full --clock-control none -k regex:mech_kernel -c 1 python bench.py
-#       --workload mech22 --cells 7168 --lanes 8 --steps 1 --warmup 1 --no-plain --no-cpu --no-e2e
-# -> 1.660 MB + 31.598 MB for 7168 cells (profiles/mech_kernel_L8_mech22_7168cells.md):
-# y, parameters and counters (~400 B) plus the write-back of the out-of-line
-# calls' stack frames.
-TRAFFIC_BYTES_PER_CELL = {"mech22": 4639.7}
+# capture (--set full, one launch) of a smaller batch of the same kernel and
+# launch shape, scaled by cells (traffic is per cell: y in and out,
+# parameters, counters, and for the lane-group kernels the write-back of the
+# out-of-line calls' stack frames):
+#   ncu --set full --clock-control none -k regex:<kernel> -c 1 -o <report> \
+#       python bench.py --workload <w> --cells <n> [--lanes <L>] --steps 1 --warmup 1 \
+#       --no-plain --no-cpu --no-e2e
+#   mech22, mech_kernel, 7168 cells, 8 lanes: 4.240 + 20.266 MB
+#   mech54, mech_kernel, 1480 cells, 32 lanes: 2.637 + 1.209 MB
+#   cosmology, thread_kernel, 2^20 cells: 26.746 + 7.812 MB
+TRAFFIC_BYTES_PER_CELL = {"mech22": 24.505856e6 / 7168, "mech54": 3.845376e6 / 1480,
+                          "cosmology": 34.557696e6 / 1048576}
 
 
 def work_model_split(kind, mech, tot, fp32_matrix=False, **kw):
