@@ -247,6 +247,54 @@ def test_step_cap_and_nonfinite_cells_are_reported_per_cell():
     np.testing.assert_array_equal(cs[good], csc[good])
 
 
+@pytest.mark.parametrize("name", ["robertson", "mech22"])
+def test_worst_cell_error_falls_with_rtol(name):
+    """The method's global error scales with rtol on the GPU as in the
+    oracle: from rtol 1e-6 to 1e-8 (atol 1e-4 rtol) the worst cell's error
+    against the rtol 1e-12 ground truth, relative to |y| over components
+    above 1e-8, falls by more than 20 (ideally 100)."""
+    need_gpu()
+    w = synth.workloads.robertson(256) if name == "robertson" else synth.workloads.mech22(96)
+    pb = oracle.problem_from_workload(w)
+    yt, _, _, _ = oracle.integrate(pb, w["y0"], w["t0"], w["tout"], 1e-12, 1e-16)
+    big = np.abs(yt) > 1e-8
+    worst = []
+    for rtol in (1e-6, 1e-8):
+        yg, cs, tot, _ = run_gpu(w, rtol=rtol, atol=rtol * 1e-4, max_steps=100000)
+        assert tot["worst_status"] == 0
+        worst.append(np.max(np.where(big, np.abs(yg - yt) / np.where(big, np.abs(yt), 1.0), 0.0)))
+    print(name, "worst relative error at rtol 1e-6, 1e-8:", worst)
+    assert worst[0] / worst[1] > 20, worst
+
+
+def test_stats_and_params_through_the_c_abi():
+    """sunb_stats (host totals and the per-cell [C, 8] counters) and
+    sunb_set_params' byte count, called through ctypes directly."""
+    import ctypes
+    need_gpu()
+    m = sb()
+    w = synth.workloads.robertson(100)
+    it = m.from_workload(w)
+    L = m.lib()
+    k = dev(w["params"])
+    for wrong in (0, 8 * 3 * 99, 8 * 3 * 101):
+        assert L.sunb_set_params(it.ctx, ctypes.c_void_p(k.data_ptr()), wrong) == m.ILL_INPUT
+        assert b"bytes" in L.sunb_last_error(it.ctx)
+    assert L.sunb_set_params(it.ctx, ctypes.c_void_p(k.data_ptr()), 8 * 3 * 100) == 0
+    it._params = k
+    y = dev(w["y0"])
+    assert L.sunb_integrate(it.ctx, ctypes.c_void_p(y.data_ptr()), 0.0, 1e5, None) == 0
+    per_cell = torch.full((100, 8), -7, dtype=torch.int32, device="cuda")
+    tot = m._Totals()
+    rc = L.sunb_stats(it.ctx, ctypes.byref(tot), ctypes.c_void_p(per_cell.data_ptr()))
+    cs = per_cell.cpu().numpy().astype(np.int64)
+    assert rc == 0 and tot.worst_status == 0 and tot.n_failed == 0
+    assert (tot.nst, tot.nfe, tot.nje, tot.nni, tot.ncf, tot.nef) == tuple(int(x) for x in cs[:, :6].sum(axis=0))
+    assert tot.max_nst == cs[:, 0].max() and np.all(cs[:, 7] == 0) and np.all(cs[:, 6] >= 1)
+    # nullable outputs
+    assert L.sunb_stats(it.ctx, None, None) == 0
+
+
 def test_invalid_arguments_are_rejected_before_launch():
     need_gpu()
     m = sb()
