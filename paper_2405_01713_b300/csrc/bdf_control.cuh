@@ -217,6 +217,7 @@ struct CellRun {
     // current step / attempt
     int last, ncf, nef;
     double dsm2, Cq, il1, gamma;
+    double etaq;          // the order-q step factor of the attempt (backends with C::kSharedEtaQ)
     double l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1];
     // current Newton solve
     int fresh, conv, setup_now, m;
@@ -408,6 +409,12 @@ struct CellRun {
             return;
         }
         dsm2 = (Cq * Cq) * c.wrms2(V_ACOR);
+        // Backends with C::kSharedEtaQ (a warp of 32 thread-per-cell cells):
+        // the cells reach the error test together, and both the failing
+        // ones and the growing ones need the order-q factor; one evaluation
+        // here, before the branch, takes one pass of the warp instead of
+        // one per path (same value: same function of the same arguments).
+        if constexpr (C::kSharedEtaQ) etaq = eta_from(dsm2, q, BIAS_Q);
         if (dsm2 >= 1.0) {            // error-test failure (accept iff ||LTE|| < 1)
             if constexpr (C::kOutlineRare) fail_error_outlined(c);
             else fail_error(c);
@@ -438,7 +445,9 @@ struct CellRun {
             s.nef++; nef++;
             if (nef >= MXNEF) { s.status = ST_ERR_FAILURE; finish(c); return; }
             if (nef < MXNEF1) {
-                double eta = eta_from(dsm2, q, BIAS_Q);
+                double eta;
+                if constexpr (C::kSharedEtaQ) eta = etaq;
+                else eta = eta_from(dsm2, q, BIAS_Q);
                 int newq = q;
                 if (q > 1) {
                     double l1m, pm;
@@ -506,7 +515,10 @@ struct CellRun {
         int newq = q;
         const double inv_q = pick(inv, q);
         const double kfac = l1 * pick(l, q) * Cq;     // h^{q+1} y^{(q+1)}/(q+1)! = kfac * Delta
-        if (BIAS_Q * BIAS_Q * dsm2 <= eta_viable2(q)) eta = eta_from(dsm2, q, BIAS_Q);
+        if (BIAS_Q * BIAS_Q * dsm2 <= eta_viable2(q)) {
+            if constexpr (C::kSharedEtaQ) eta = etaq;
+            else eta = eta_from(dsm2, q, BIAS_Q);
+        }
         if (qwait == 0) {
             double em = 0.0, ep = 0.0;
             if (q > 1) {

@@ -248,6 +248,8 @@ struct GroupCell : KrylovScratch<KRY> {
     static constexpr bool kNewtonLoop = false;
     // the starting step and the failure paths out of line (see CellRun)
     static constexpr bool kOutlineRare = true;
+    // the order-q step factor only where a path needs it (see CellRun::post)
+    static constexpr bool kSharedEtaQ = false;
     // matrix-free GMRES linear solves in the scratch kry instead of LU
     // factors (a separate kernel, so the direct kernel carries none of it)
     static constexpr bool kKrylov = KRY;

@@ -33,6 +33,9 @@ struct RobertsonProblem {
         J[2][0] = 0.0;  J[2][1] = 2.0 * k2 * y[1];               J[2][2] = 0.0;
     }
     static constexpr bool kFusedJac = false;   // J costs extra work: only at set-ups
+    // small batches spread about two cells per warp: evaluating the
+    // order-q factor for every cell would add latency (+10 % measured)
+    static constexpr bool kSharedEtaQ = false;
 };
 
 // Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
@@ -101,6 +104,8 @@ struct CosmologyProblem {
     }
     // f and df/de come from one evaluation
     static constexpr bool kFusedJac = true;
+    // full warps of cells: one shared evaluation of the order-q factor (-5 %)
+    static constexpr bool kSharedEtaQ = true;
     __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
     {
         eval(y[0], f[0], J[0][0]);
@@ -160,6 +165,9 @@ struct ThreadCell : ThreadTape<REC> {
     // logic (cheap f, costly control) then stays aligned across the warp
     static constexpr bool kNewtonLoop = true;
     static constexpr bool kOutlineRare = false;
+    // the order-q step factor evaluated once before the error test's branch
+    // (see CellRun::post) where the problem's batches fill whole warps
+    static constexpr bool kSharedEtaQ = Prob::kSharedEtaQ;
     // linear solves with the LU factors (no Krylov variant)
     static constexpr bool kKrylov = false;
     Prob prob;
