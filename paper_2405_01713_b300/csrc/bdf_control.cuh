@@ -217,7 +217,8 @@ struct CellRun {
     // current step / attempt
     int last, ncf, nef;
     double dsm2, Cq, il1, gamma;
-    double etaq;          // the order-q step factor of the attempt (backends with C::kSharedEtaQ)
+    double etaq, emq;     // the order-q and order-(q-1) step factors of the attempt
+                          // (backends with C::kSharedEtaQ; emq 0 where not needed)
     double l[QMAX + 1], xi[QMAX + 1], inv[QMAX + 1];
     // current Newton solve
     int fresh, conv, setup_now, m;
@@ -414,7 +415,26 @@ struct CellRun {
         // ones and the growing ones need the order-q factor; one evaluation
         // here, before the branch, takes one pass of the warp instead of
         // one per path (same value: same function of the same arguments).
-        if constexpr (C::kSharedEtaQ) etaq = eta_from(dsm2, q, BIAS_Q);
+        if constexpr (C::kSharedEtaQ) {
+            etaq = eta_from(dsm2, q, BIAS_Q);
+            // likewise the order q-1 factor, which the first two error-test
+            // failures of a step and the order selection that comes due
+            // after an accepted step both need (the failures from the
+            // predicted z_q, which the prediction leaves unchanged, the
+            // selection from the corrected z_q + l_q Delta)
+            emq = 0.0;
+            if (q > 1) {
+                const bool fail = dsm2 >= 1.0;
+                if (fail ? (nef + 1 < MXNEF1) : (!last && qwait == 1)) {
+                    double l1m, pm;
+                    lower_order_sums(q, inv, xi, l1m, pm);
+                    const double f = pm * rcp(l1m);
+                    const double d2 = (fail ? c.wrms2(q) : c.wrms2_corrected(q, pick(l, q))) * f * f;
+                    if (fail || BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1))
+                        emq = eta_from(d2, q - 1, BIAS_QM1);
+                }
+            }
+        }
         if (dsm2 >= 1.0) {            // error-test failure (accept iff ||LTE|| < 1)
             if constexpr (C::kOutlineRare) fail_error_outlined(c);
             else fail_error(c);
@@ -450,10 +470,15 @@ struct CellRun {
                 else eta = eta_from(dsm2, q, BIAS_Q);
                 int newq = q;
                 if (q > 1) {
-                    double l1m, pm;
-                    lower_order_sums(q, inv, xi, l1m, pm);
-                    const double f = pm * rcp(l1m);
-                    const double em = eta_from(c.wrms2(q) * f * f, q - 1, BIAS_QM1);
+                    double em;
+                    if constexpr (C::kSharedEtaQ) {
+                        em = emq;
+                    } else {
+                        double l1m, pm;
+                        lower_order_sums(q, inv, xi, l1m, pm);
+                        const double f = pm * rcp(l1m);
+                        em = eta_from(c.wrms2(q) * f * f, q - 1, BIAS_QM1);
+                    }
                     if (em > eta) { eta = em; newq = q - 1; }
                 }
                 eta = fmin(ETA_MAX_EF, fmax(ETA_MIN_EF, eta));
@@ -522,11 +547,15 @@ struct CellRun {
         if (qwait == 0) {
             double em = 0.0, ep = 0.0;
             if (q > 1) {
-                double l1m, pm;
-                lower_order_sums(q, inv, xi, l1m, pm);
-                const double f = pm * rcp(l1m);
-                const double d2 = c.wrms2(q) * f * f;
-                if (BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1)) em = eta_from(d2, q - 1, BIAS_QM1);
+                if constexpr (C::kSharedEtaQ) {
+                    em = emq;
+                } else {
+                    double l1m, pm;
+                    lower_order_sums(q, inv, xi, l1m, pm);
+                    const double f = pm * rcp(l1m);
+                    const double d2 = c.wrms2(q) * f * f;
+                    if (BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1)) em = eta_from(d2, q - 1, BIAS_QM1);
+                }
             }
             if (q < qmax && have_ks) {
                 double rq = 1.0;

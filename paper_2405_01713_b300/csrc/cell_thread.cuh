@@ -220,6 +220,23 @@ struct ThreadCell : ThreadTape<REC> {
         }
         return s * (1.0 / N);
     }
+    // squared WRMS norm of the corrected column q, z_q + lq Delta, before
+    // the correction is applied (q a runtime order, selected by predicate)
+    __device__ __forceinline__ double wrms2_corrected(int q, double lq) const
+    {
+        double s = 0.0;
+#pragma unroll
+        for (int j = 1; j <= QMAX; ++j) {
+            if (j == q) {
+#pragma unroll
+                for (int i = 0; i < N; ++i) {
+                    const double t = (v[j][i] + lq * v[V_ACOR][i]) * v[V_W][i];
+                    s += t * t;
+                }
+            }
+        }
+        return s * (1.0 / N);
+    }
     __device__ __forceinline__ double wrms2_lin(double a, int va, double b, int vb) const
     {
         double s = 0.0;
