@@ -83,10 +83,10 @@ def jac_matrix_flops(mech):
 #       --no-plain --no-cpu --no-e2e
 #   mech22, mech_kernel, 7168 cells, 8 lanes: 4.240 + 20.266 MB
 #   mech54, mech_kernel, 1480 cells, 32 lanes: 2.637 + 1.209 MB
-#   cosmology, thread_kernel, 2^20 cells: 26.766 + 8.232 MB (--metrics
+#   cosmology, thread_kernel, 2^20 cells: 27.141 + 7.857 MB (--metrics
 #       dram__bytes_read.sum,dram__bytes_write.sum instead of --set full)
 TRAFFIC_BYTES_PER_CELL = {"mech22": 24.505856e6 / 7168, "mech54": 3.845376e6 / 1480,
-                          "cosmology": 34.998784e6 / 1048576}
+                          "cosmology": 34.997504e6 / 1048576}
 
 
 def work_model_split(kind, mech, tot, fp32_matrix=False, **kw):

@@ -364,8 +364,11 @@ struct CellRun {
             start_newton(c);
         }
         // modified Newton iterations (Eq. stop_newton) until convergence,
-        // divergence or MAXCOR: all of them in this superstep when the
-        // backend asks for it (C::kNewtonLoop), else one per superstep
+        // divergence or MAXCOR, at most C::kNewtonPerSuperstep of them in
+        // this superstep; a cell that needs more continues in the next
+        // superstep, at the same f call site as the other cells' first
+        // iterations (the arithmetic does not depend on where it stops)
+        int iters_here = 0;
         while (phase == PH_NEWTON) {
             const int ok = c.newton_f(setup_now != 0, gamma);
             s.nfe++;
@@ -393,7 +396,7 @@ struct CellRun {
                 }
             }
             if (done) phase = PH_POST;
-            if (!C::kNewtonLoop) break;
+            if (++iters_here >= C::kNewtonPerSuperstep) break;
         }
         if (phase == PH_POST) post(c);
     }

@@ -245,7 +245,7 @@ struct GroupCell : KrylovScratch<KRY> {
     // one Newton iteration per superstep: a group that needs another
     // iteration takes it in the next superstep, at the same f call site as
     // the first iterations of the other groups of its warp
-    static constexpr bool kNewtonLoop = false;
+    static constexpr int kNewtonPerSuperstep = 1;
     // the starting step and the failure paths out of line (see CellRun)
     static constexpr bool kOutlineRare = true;
     // the order-q step factor only where a path needs it (see CellRun::post)

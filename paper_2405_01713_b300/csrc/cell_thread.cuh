@@ -36,6 +36,9 @@ struct RobertsonProblem {
     // small batches spread about two cells per warp: evaluating the
     // order-q factor for every cell would add latency (+10 % measured)
     static constexpr bool kSharedEtaQ = false;
+    // all Newton iterations of an attempt in one superstep (a cap of two
+    // cost the spread batches 2 %)
+    static constexpr int kNewtonPerSuperstep = MAXCOR;
 };
 
 // Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
@@ -106,6 +109,11 @@ struct CosmologyProblem {
     static constexpr bool kFusedJac = true;
     // full warps of cells: one shared evaluation of the order-q factor (-5 %)
     static constexpr bool kSharedEtaQ = true;
+    // at most two Newton iterations per superstep: a warp no longer waits
+    // for its slowest cell's third iteration, which runs in the next
+    // superstep beside the other cells' first ones (-2.4 %; one per
+    // superstep was 23 % slower: the control phases diverge)
+    static constexpr int kNewtonPerSuperstep = 2;
     __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
     {
         eval(y[0], f[0], J[0][0]);
@@ -161,9 +169,10 @@ template <> struct ThreadTape<true> {
 template <class Prob, bool REC = false>
 struct ThreadCell : ThreadTape<REC> {
     static constexpr int N = Prob::N;
-    // all Newton iterations of an attempt in one superstep: the control
-    // logic (cheap f, costly control) then stays aligned across the warp
-    static constexpr bool kNewtonLoop = true;
+    // Newton iterations per superstep (the problem's choice): most or all
+    // of an attempt's, so that the control logic (cheap f, costly control)
+    // stays aligned across the warp
+    static constexpr int kNewtonPerSuperstep = Prob::kNewtonPerSuperstep;
     static constexpr bool kOutlineRare = false;
     // the order-q step factor evaluated once before the error test's branch
     // (see CellRun::post) where the problem's batches fill whole warps
