@@ -200,6 +200,9 @@ __device__ __forceinline__ bool start_cell(C &c, const Controls &ctl, CellStats 
 // nested loops.  A cell's arithmetic is exactly that of the sequential
 // algorithm (bdf_cell below runs it sequentially).
 enum Phase : int {
+    // the two f evaluations of a cell's start, for backends with
+    // C::kFoldedStart (CellRun::begin_folded); below PH_STEP
+    PH_START0 = -2, PH_START1 = -1,
     PH_STEP = 0, PH_ATTEMPT = 1, PH_SETUP = 2, PH_NEWTON = 3, PH_POST = 4,
     PH_DONE = 5,    // finished; the caller collects s and may begin another cell
     PH_EXIT = 6     // no cell left for this thread or group (set by run_cells)
@@ -238,8 +241,70 @@ struct CellRun {
     // for thread-per-cell cells they are too frequent to pay a call.
     __device__ __forceinline__ void begin(C &c, const Controls &ctl)
     {
-        if constexpr (C::kOutlineRare) begin_outlined(c, ctl);
+        if constexpr (C::kFoldedStart) begin_folded(c, ctl);
+        else if constexpr (C::kOutlineRare) begin_outlined(c, ctl);
         else begin_body(c, ctl);
+    }
+
+    // Backends with C::kFoldedStart (a thread per cell, where the cells of a
+    // warp begin at different supersteps): the start's two f evaluations
+    // run at the Newton iterations' f call site, in phases START0 and
+    // START1, so that a beginning cell joins its warp's evaluations instead
+    // of running its own while the other 31 lanes wait.  The arithmetic is
+    // begin_body's: f(t0, y0) arrives in V_F and is kept in V_ACOR while
+    // f(t0 + h0, y0 + h0 f0) arrives in V_F; between the phases h holds h0
+    // and delp2 holds ||f0||^2 (both unused until the first step).
+    __device__ __forceinline__ void begin_folded(C &c, const Controls &ctl)
+    {
+        tout = ctl.tout;
+        qmax = ctl.max_order < 1 ? 1 : (ctl.max_order > QMAX ? QMAX : ctl.max_order);
+        s.nst = s.nfe = s.nje = s.nni = s.ncf = s.nef = 0;
+        s.qlast = 1;
+        s.status = ST_SUCCESS;
+        q = 1;
+        c.load_y(V_Z0);
+        if (!(tout > ctl.t0)) { finish(c); return; }
+        c.newton_init();           // V_Y = y0
+        setup_now = 0;
+        phase = PH_START0;
+    }
+    __device__ __forceinline__ void start_after_f(C &c, const Controls &ctl)
+    {
+        const double t0 = ctl.t0, span = tout - t0;
+        if (phase == PH_START0) {   // V_F = f(t0, y0)
+            if (!c.all_finite(V_F) || !c.all_finite(V_Z0)) {
+                s.status = ST_NONFINITE;
+                finish(c);
+                return;
+            }
+            c.set_weights(V_Z0, ctl.rtol);
+            const double d0 = c.wrms2(V_Z0), d1 = c.wrms2(V_F);   // squared
+            double h0 = (d0 < 1e-10 || d1 < 1e-10) ? 1e-6 * span : 0.01 * sqrt(d0 * rcp(d1));
+            if (h0 > span) h0 = span;
+            c.axpby(V_Y, 1.0, V_Z0, h0, V_F);
+            c.copy(V_ACOR, V_F);
+            h = h0;
+            delp2 = d1;
+            phase = PH_START1;
+            return;
+        }
+        // V_F = f(t0 + h0, y0 + h0 f0), V_ACOR = f0
+        const double h0 = h, d1 = delp2;
+        const double rh0 = rcp(h0);
+        const double d2 = c.wrms2_lin(rh0, V_F, -rh0, V_ACOR);
+        const double dm = fmax(d1, d2);
+        double h1 = (dm <= 1e-30) ? fmax(1e-6 * span, h0 * 1e-3) : sqrt(0.01 * rcp(sqrt(dm)));
+        h = fmin(100.0 * h0, h1);
+        if (!(h > 0.0)) h = 1e-6 * span;
+        h = fmin(h, span);
+        c.scale(V_Z1, h, V_ACOR);
+        c.rec_init(h);
+        t = t0;
+        qwait = 2; have_M = 0; force_setup = 1; nst_lastsetup = 0; have_ks = 0; nsame = 0;
+#pragma unroll
+        for (int i = 0; i <= QMAX; ++i) hist[i] = 0.0;
+        gamma_M = 0.0; etamax = ETA_MAX_FIRST; h_ks = 0.0;
+        phase = PH_STEP;
     }
     __device__ __noinline__ void begin_outlined(C &c, const Controls &ctl) { begin_body(c, ctl); }
     __device__ __forceinline__ void begin_body(C &c, const Controls &ctl)
@@ -368,10 +433,18 @@ struct CellRun {
         // this superstep; a cell that needs more continues in the next
         // superstep, at the same f call site as the other cells' first
         // iterations (the arithmetic does not depend on where it stops)
+        // (with C::kFoldedStart the same f call serves the start phases)
         int iters_here = 0;
-        while (phase == PH_NEWTON) {
+        while (phase == PH_NEWTON || (C::kFoldedStart && phase < 0)) {
             const int ok = c.newton_f(setup_now != 0, gamma);
             s.nfe++;
+            if constexpr (C::kFoldedStart) {
+                if (phase < 0) {
+                    start_after_f(c, ctl);
+                    if (++iters_here >= C::kNewtonPerSuperstep) break;
+                    continue;
+                }
+            }
             if (setup_now) s.nfe += c.f_per_setup();
             if (setup_now) { have_M = ok; setup_now = 0; }
             bool done = false;

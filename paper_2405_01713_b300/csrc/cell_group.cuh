@@ -250,6 +250,9 @@ struct GroupCell : KrylovScratch<KRY> {
     static constexpr bool kOutlineRare = true;
     // the order-q step factor only where a path needs it (see CellRun::post)
     static constexpr bool kSharedEtaQ = false;
+    // cells begin through begin_body (out of line): a lane group's start
+    // evaluations are group-wide calls of their own
+    static constexpr bool kFoldedStart = false;
     // matrix-free GMRES linear solves in the scratch kry instead of LU
     // factors (a separate kernel, so the direct kernel carries none of it)
     static constexpr bool kKrylov = KRY;

@@ -39,6 +39,8 @@ struct RobertsonProblem {
     // all Newton iterations of an attempt in one superstep (a cap of two
     // cost the spread batches 2 %)
     static constexpr int kNewtonPerSuperstep = MAXCOR;
+    // cells of a one-wave launch all begin together: the start stays inline
+    static constexpr bool kFoldedStart = false;
 };
 
 // Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
@@ -90,10 +92,16 @@ struct CosmologyProblem {
         while (lo > 0 && !(x[lo] <= lnT)) --lo;
         while (lo < n - 2 && x[lo + 1] <= lnT) ++lo;
         const double sl = tab->slope[lo];
-        const double lam = fexp(tab->lnLam[lo] + sl * (lnT - x[lo]), tab->exptab);
-        const double heat = tab->gamma_heat * fexp(-0.7 * (lnT - LN1E4), tab->exptab);
-        f = F + rho * (heat - lam);
-        dfde = floor ? 0.0 : rho * (-0.7 * heat - sl * lam) * rcp(T);
+        // Every rounding is spelled out (fma, or __dmul_rn, which is never
+        // merged into a multiply-add): where a sum of products leaves the
+        // compiler a choice of which product to fuse, or a product feeds two
+        // sums, the choice may differ between the kernels that integrate
+        // cosmology cells, and a cell's result would depend on which kernel
+        // took it.
+        const double lam = fexp(fma(sl, lnT - x[lo], tab->lnLam[lo]), tab->exptab);
+        const double heat = __dmul_rn(tab->gamma_heat, fexp(-0.7 * (lnT - LN1E4), tab->exptab));
+        f = fma(rho, heat - lam, F);
+        dfde = floor ? 0.0 : rho * fma(-0.7, heat, -(sl * lam)) * rcp(T);
     }
     __device__ __forceinline__ void rhs(const double *y, double *f) const
     {
@@ -114,6 +122,9 @@ struct CosmologyProblem {
     // superstep beside the other cells' first ones (-2.4 %; one per
     // superstep was 23 % slower: the control phases diverge)
     static constexpr int kNewtonPerSuperstep = 2;
+    // a cell's start shares its warp's f evaluations (CellRun::begin_folded):
+    // queue-fed warps begin cells at different supersteps
+    static constexpr bool kFoldedStart = true;
     __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
     {
         eval(y[0], f[0], J[0][0]);
@@ -177,6 +188,7 @@ struct ThreadCell : ThreadTape<REC> {
     // the order-q step factor evaluated once before the error test's branch
     // (see CellRun::post) where the problem's batches fill whole warps
     static constexpr bool kSharedEtaQ = Prob::kSharedEtaQ;
+    static constexpr bool kFoldedStart = Prob::kFoldedStart;
     // linear solves with the LU factors (no Krylov variant)
     static constexpr bool kKrylov = false;
     Prob prob;
@@ -214,7 +226,7 @@ struct ThreadCell : ThreadTape<REC> {
     __device__ __forceinline__ void set_weights(int a, double rtol)
     {
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[V_W][i] = rcp(rtol * fabs(v[a][i]) + atol[i]);
+        for (int i = 0; i < N; ++i) v[V_W][i] = rcp(fma(rtol, fabs(v[a][i]), atol[i]));
     }
     // squared WRMS norm of slot a; a may be a runtime Nordsieck column
     __device__ __forceinline__ double wrms2(int a) const
@@ -239,19 +251,21 @@ struct ThreadCell : ThreadTape<REC> {
             if (j == q) {
 #pragma unroll
                 for (int i = 0; i < N; ++i) {
-                    const double t = (v[j][i] + lq * v[V_ACOR][i]) * v[V_W][i];
+                    const double t = fma(lq, v[V_ACOR][i], v[j][i]) * v[V_W][i];
                     s += t * t;
                 }
             }
         }
         return s * (1.0 / N);
     }
+    // (a x + b y with the product a x fused, in every kernel alike: the sum
+    // of two products leaves the compiler a choice otherwise)
     __device__ __forceinline__ double wrms2_lin(double a, int va, double b, int vb) const
     {
         double s = 0.0;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double t = (a * v[va][i] + b * v[vb][i]) * v[V_W][i];
+            const double t = fma(a, v[va][i], b * v[vb][i]) * v[V_W][i];
             s += t * t;
         }
         return s * (1.0 / N);
@@ -259,7 +273,12 @@ struct ThreadCell : ThreadTape<REC> {
     __device__ __forceinline__ void axpby(int o, double a, int va, double b, int vb)
     {
 #pragma unroll
-        for (int i = 0; i < N; ++i) v[o][i] = a * v[va][i] + b * v[vb][i];
+        for (int i = 0; i < N; ++i) v[o][i] = fma(b, v[vb][i], a * v[va][i]);   // b y fused
+    }
+    __device__ __forceinline__ void copy(int o, int va)
+    {
+#pragma unroll
+        for (int i = 0; i < N; ++i) v[o][i] = v[va][i];
     }
     __device__ __forceinline__ void scale(int o, double a, int va)
     {
@@ -303,7 +322,7 @@ struct ThreadCell : ThreadTape<REC> {
         for (int j = 0; j <= QMAX; ++j)
             if (j <= q)
 #pragma unroll
-                for (int i = 0; i < N; ++i) v[j][i] += l[j] * v[V_ACOR][i];
+                for (int i = 0; i < N; ++i) v[j][i] = fma(l[j], v[V_ACOR][i], v[j][i]);
     }
     __device__ __forceinline__ void order_increase(int q, const double *l, double inv_xi)
     {
@@ -358,14 +377,14 @@ struct ThreadCell : ThreadTape<REC> {
     {
 #pragma unroll
         for (int i = 0; i < N; ++i)
-            v[V_DEL][i] = (h * v[V_F][i] - v[V_Z1][i]) * il1 - v[V_ACOR][i];
+            v[V_DEL][i] = fma(fma(h, v[V_F][i], -v[V_Z1][i]), il1, -v[V_ACOR][i]);
     }
     __device__ __forceinline__ double newton_update(double c)
     {
         double s = 0.0;
 #pragma unroll
         for (int i = 0; i < N; ++i) {
-            const double d = v[V_DEL][i] * c;
+            const double d = __dmul_rn(v[V_DEL][i], c);   // feeds two sums: never fused
             v[V_ACOR][i] += d;
             v[V_Y][i] = v[V_Z0][i] + v[V_ACOR][i];
             const double t = d * v[V_W][i];

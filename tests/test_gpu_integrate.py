@@ -193,6 +193,26 @@ def test_mixed_batch_matches_single_kind_runs():
         assert np.all(cs[:, 7] == 0) and cs.shape[0] == 3064
 
 
+@pytest.mark.parametrize("precision", [0, 1])
+def test_mixed_cosmology_cells_equal_a_cosmology_launch(precision):
+    """A cosmology cell of a mixed launch is integrated either by the
+    mechanism kernel's tail (threads whose group found no mechanism cell
+    left) or by the thread-per-cell kernel that follows, whichever takes it
+    from the queue first.  Both run the same arithmetic, so the cosmology
+    cells give, byte for byte, the states and counters of a cosmology-only
+    launch, whatever the split and from one run to the next."""
+    need_gpu()
+    nc = 200000
+    w = synth.workloads.mixed(n_cosmo=nc, n_mech=512)
+    yc, csc, _, _ = run_gpu(synth.workloads.cosmology(nc))
+    for lanes in (8, 32):
+        for _ in range(2):
+            yg, cs, tot, _ = run_gpu(w, lanes=lanes, precision=precision)
+            assert tot["worst_status"] == 0
+            np.testing.assert_array_equal(yg[:nc], yc.ravel())
+            np.testing.assert_array_equal(cs[:nc], csc)
+
+
 @pytest.mark.parametrize("lanes", [8, 16, 32])
 def test_ragged_batches(lanes):
     """Batch sizes that leave partial warps and partial CTAs give, cell by
