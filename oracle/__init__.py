@@ -1,8 +1,9 @@
 """CPU oracle (TEST INFRASTRUCTURE ONLY).
 
-A plain FP64 C implementation of the batched BDF integrator, its right-hand
-sides, Jacobians and LU, and of the variants it is compared with (GMRES
-linear solves, an explicit Runge-Kutta method), loaded with ctypes.  Only ``tests/``,
+A plain FP64 C implementation of the batched BDF integrator (its step-size
+factors, a heuristic, in single precision), its right-hand sides, Jacobians
+and LU, and of the variants it is compared with (GMRES linear solves, an
+explicit Runge-Kutta method), loaded with ctypes.  Only ``tests/``,
 ``__graft_entry__.smoke()`` and the CPU-baseline leg of ``bench.py`` may
 import this package; the CUDA library never calls it.
 

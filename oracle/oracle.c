@@ -1,6 +1,7 @@
 /* CPU oracle for the batched BDF integrator: TEST INFRASTRUCTURE ONLY.
  *
- * Plain C, FP64, one cell at a time (OpenMP only distributes independent
+ * Plain C, FP64 (the step-size factors, a heuristic, in single precision:
+ * see eta_from), one cell at a time (OpenMP only distributes independent
  * cells).  Only the tests, smoke() and the benchmark's CPU-baseline leg may
  * load it; the CUDA library shares no code with it.
  *
@@ -32,8 +33,8 @@
  *  - matrix rebuild (fresh J, M = I - gamma J, LU) when 20 steps have passed
  *    since the last one, when |gamma/gamma_M - 1| > 0.3, or after a Newton
  *    failure; a stale matrix scales each correction by 2/(1 + gamma/gamma_M);
- *  - step factors eta_p = 1/((b_p ||E_p||)^(1/(p+1)) + 1e-6) with biases
- *    6 (q-1), 6 (q), 10 (q+1); no change below 1.5; growth capped at 1e4 on
+ *  - step factors eta_p = 1/((b_p ||E_p||)^(1/(p+1)) + 1e-6), in single
+ *    precision, with biases 6 (q-1), 6 (q), 10 (q+1); no change below 1.5; growth capped at 1e4 on
  *    the first step and 10 afterwards, and at 1 right after a failed attempt;
  *    order changes considered after q+1 steps at the current order;
  *  - error-test failure: eta in [0.1, 0.9], lower order when that allows a
@@ -291,9 +292,18 @@ static void rescale(int q, int n, double *z, double eta)
     }
 }
 
+/* Step factor eta_p = 1/((b ||E_p||)^(1/(p+1)) + 1e-6), in single
+ * precision: L = log2(b ||E_p||) rounded to float, r = 2^(L/(p+1)) and
+ * eta = 1/(r + 1e-6) in float.  The paper fixes no precision for this
+ * heuristic, which only scales h; the CUDA path computes it in single
+ * precision, and the decisions it makes (keep h below 1.5, the order of the
+ * largest factor) are taken here in the same precision.  ||E|| = 0 gives
+ * L = -inf and eta = 1e6 (above every growth cap). */
 static double eta_from(double dsm, int p, double bias)
 {
-    return 1.0 / (pow(bias * dsm, 1.0 / (p + 1)) + 1e-6);
+    const float L = (float)log2(bias * dsm);
+    const float r = exp2f(L / (float)(p + 1));
+    return (double)(1.0f / (r + 1e-6f));
 }
 
 /* Step factor and order after an accepted step at order q (Sec. 2: the

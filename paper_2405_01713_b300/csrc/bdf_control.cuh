@@ -20,8 +20,9 @@
 //  * the Newton matrix is rebuilt after 20 steps, when gamma moved by more
 //    than 30 %, or after a failure; a stale matrix scales corrections by
 //    2/(1 + gamma/gamma_M);
-//  * step factors 1/((b ||E_p||)^(1/(p+1)) + 1e-6), biases 6/6/10 for
-//    orders q-1/q/q+1, threshold 1.5, caps 1e4 (first step) / 10 / 1
+//  * step factors 1/((b ||E_p||)^(1/(p+1)) + 1e-6) in single precision,
+//    biases 6/6/10 for orders q-1/q/q+1, threshold 1.5, caps 1e4 (first
+//    step) / 10 / 1
 //    (after a failure); order change considered after q+1 steps at q;
 //  * failures: error test -> eta in [0.1, 0.9] (or order q-1), third
 //    failure -> eta 0.1 at order 1 (reached by lowering the order of the
@@ -82,14 +83,35 @@ __device__ __forceinline__ double pick(const double *a, int k)
 }
 
 // 1/(p+1), p = 0..6
-__constant__ double INV_P1[7] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 1.0 / 5.0, 1.0 / 6.0, 1.0 / 7.0};
+__constant__ float INV_P1F[7] = {1.0f, 1.0f / 2.0f, 1.0f / 3.0f, 1.0f / 4.0f, 1.0f / 5.0f, 1.0f / 6.0f,
+                                 1.0f / 7.0f};
 
-// Step factor from a squared WRMS error norm at order p.
-__device__ __forceinline__ double eta_from(double d2, int p, double bias)
+// Step factor eta_p = 1/((b ||E_p||)^(1/(p+1)) + 1e-6) from the squared WRMS
+// norm d2 = ||E_p||^2, in single precision: L = log2(b ||E_p||) rounded to
+// float, r = 2^(L/(p+1)), eta = 1/(r + 1e-6).  The factor is a heuristic
+// that only scales h; the decisions it makes (keep h below 1.5, the order of
+// the largest factor) are taken in this precision, and the oracle takes them
+// in the same one.  L = log2 b + (e + log2 m)/2 for d2 = 2^e m, e and the
+// leading 23 bits of m read from the double's bits: the whole double range
+// without an FP64 instruction (the FP64 pipe is the kernels' bound; the
+// float functions run on the FP32 pipe).  d2 = 0 or subnormal gives L = -inf
+// (eta = 1e6, above every growth cap), d2 = inf gives L = +inf (eta = 0).
+__device__ __forceinline__ double eta_from(double d2, int p, float bias)
 {
-    // (bias * sqrt(d2))^(1/(p+1)) = exp(0.5 * log(bias^2 d2) / (p+1))
-    double r = fexp(0.5 * flog(bias * bias * d2) * INV_P1[p], g_exp_tab);
-    return rcp(r + 1e-6);
+    const int hi = __double2hiint(d2);
+    float L;
+    if (hi >= 0x7ff00000) {
+        L = __int_as_float(0x7f800000);
+    } else if (hi < 0x00100000) {
+        L = -__int_as_float(0x7f800000);
+    } else {
+        const int e = (hi >> 20) - 1023;
+        const float m = __int_as_float(0x3f800000 | ((hi & 0x000fffff) << 3) |
+                                       (int)((unsigned)__double2loint(d2) >> 29));   // [1, 2)
+        L = fmaf(0.5f, (float)e + log2f(m), log2f(bias));
+    }
+    const float r = exp2f(L * INV_P1F[p]);
+    return (double)(1.0f / (r + 1e-6f));
 }
 
 // sum_{i<q-1} inv[i] and prod_{i<q-1} xi[i] (the order q-1 estimate's
@@ -136,19 +158,6 @@ __constant__ double GEAR_INV[QMAX + 1] = {1.0, 1.0 / 2.0, 1.0 / 3.0, 1.0 / 4.0, 
 // 1/l_1 = 1/H_q (H_q harmonic numbers) and C_q = 1/(1 + H_q (q+1))
 __constant__ double GEAR_IL1[QMAX + 1] = {1.0, 1.0, 2.0 / 3.0, 6.0 / 11.0, 12.0 / 25.0, 60.0 / 137.0};
 __constant__ double GEAR_CQ[QMAX + 1] = {1.0, 1.0 / 3.0, 2.0 / 11.0, 6.0 / 50.0, 12.0 / 137.0, 60.0 / 882.0};
-
-// eta_p >= 1.5 exactly when bias^2 * ||E_p||^2 <= (2/3 - 1e-6)^(2(p+1)):
-// the step-size choice takes the power only when a change can follow.  The
-// thresholds for p = 0..6, evaluated by the compiler.
-constexpr double viable2_value(int p)
-{
-    double r = 1.0;
-    for (int i = 0; i < 2 * (p + 1); ++i) r *= 2.0 / 3.0 - 1e-6;
-    return r;
-}
-__constant__ double ETA_VIABLE2[7] = {viable2_value(0), viable2_value(1), viable2_value(2), viable2_value(3),
-                                      viable2_value(4), viable2_value(5), viable2_value(6)};
-__device__ __forceinline__ double eta_viable2(int p) { return ETA_VIABLE2[p]; }
 
 // The first steps of a cell for the explicit controller, the same as
 // CellRun::begin_body's: y0 into V_Z0, f(t0, y0) into V_F, the weights from
@@ -506,8 +515,7 @@ struct CellRun {
                     lower_order_sums(q, inv, xi, l1m, pm);
                     const double f = pm * rcp(l1m);
                     const double d2 = (fail ? c.wrms2(q) : c.wrms2_corrected(q, pick(l, q))) * f * f;
-                    if (fail || BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1))
-                        emq = eta_from(d2, q - 1, BIAS_QM1);
+                    emq = eta_from(d2, q - 1, BIAS_QM1);
                 }
             }
         }
@@ -616,10 +624,8 @@ struct CellRun {
         int newq = q;
         const double inv_q = pick(inv, q);
         const double kfac = l1 * pick(l, q) * Cq;     // h^{q+1} y^{(q+1)}/(q+1)! = kfac * Delta
-        if (BIAS_Q * BIAS_Q * dsm2 <= eta_viable2(q)) {
-            if constexpr (C::kSharedEtaQ) eta = etaq;
-            else eta = eta_from(dsm2, q, BIAS_Q);
-        }
+        if constexpr (C::kSharedEtaQ) eta = etaq;
+        else eta = eta_from(dsm2, q, BIAS_Q);
         if (qwait == 0) {
             double em = 0.0, ep = 0.0;
             if (q > 1) {
@@ -630,7 +636,7 @@ struct CellRun {
                     lower_order_sums(q, inv, xi, l1m, pm);
                     const double f = pm * rcp(l1m);
                     const double d2 = c.wrms2(q) * f * f;
-                    if (BIAS_QM1 * BIAS_QM1 * d2 <= eta_viable2(q - 1)) em = eta_from(d2, q - 1, BIAS_QM1);
+                    em = eta_from(d2, q - 1, BIAS_QM1);
                 }
             }
             if (q < qmax && have_ks) {
@@ -644,7 +650,7 @@ struct CellRun {
                 const double l1p = l1 + inv_q;
                 const double f = pp * rcp(l1p * (q + 2));
                 const double d2 = c.wrms2_lin(kfac, V_ACOR, -rq, V_KS) * f * f;
-                if (BIAS_QP1 * BIAS_QP1 * d2 <= eta_viable2(q + 1)) ep = eta_from(d2, q + 1, BIAS_QP1);
+                ep = eta_from(d2, q + 1, BIAS_QP1);
             }
             if (em > eta && em >= ep) { eta = em; newq = q - 1; }
             else if (ep > eta) { eta = ep; newq = q + 1; }

@@ -118,7 +118,7 @@ constexpr double ETA_MAX_EF = 0.9;
 constexpr double ETA_THRESH = 1.5;     // below this the step is kept
 constexpr double ETA_MAX_FIRST = 1e4;  // growth cap after the first step
 constexpr double ETA_MAX = 10.0;       // growth cap afterwards
-constexpr double BIAS_QM1 = 6.0, BIAS_Q = 6.0, BIAS_QP1 = 10.0;
+constexpr float BIAS_QM1 = 6.0f, BIAS_Q = 6.0f, BIAS_QP1 = 10.0f;   // (single precision: eta_from)
 
 enum Status : int32_t {
     ST_SUCCESS = 0, ST_TOO_MUCH_WORK = -1, ST_ERR_FAILURE = -3,
