@@ -519,17 +519,50 @@ struct CellRun {
                 }
             }
         }
+        Tail tl;
         if (dsm2 >= 1.0) {            // error-test failure (accept iff ||LTE|| < 1)
-            if constexpr (C::kOutlineRare) fail_error_outlined(c);
-            else fail_error(c);
-            return;
+            if constexpr (C::kOutlineRare) fail_error_outlined(c, tl);
+            else fail_error(c, tl);
+        } else {
+            accept_step(c, tl);
         }
-        accept_step(c);
+        if constexpr (C::kSharedEtaQ) end_attempt(c, tl);
+    }
+
+    // The common end of an error-test failure and an accepted step, for
+    // backends with C::kSharedEtaQ, whose warps nearly always hold cells on
+    // both paths: the paths record an order decrease from order dec (0:
+    // none) and a rescale by eta (1: none), and end_attempt applies them
+    // once after the branch, in the order the paths would (decrease, then
+    // h *= eta and the rescale at the new order), then the step-size
+    // underflow check of a failure.  Other backends apply them in the paths.
+    struct Tail {
+        int dec = 0, fail = 0;
+        double eta = 1.0;
+    };
+    __device__ __forceinline__ void end_attempt(C &c, const Tail &tl)
+    {
+        if (tl.dec) {
+            // the nodes of the polynomial the decrease keeps: xi_i after an
+            // accepted step; after a failure (t_n - t_{n-1-i})/h_n, the sums
+            // of the previous steps, = xi_{i+1} - 1 of the failed attempt
+            double nodes[QMAX], e[QMAX + 1];
+#pragma unroll
+            for (int i = 0; i < QMAX - 1; ++i) nodes[i] = tl.fail ? xi[i + 1] - 1.0 : xi[i];
+            nodes[QMAX - 1] = 0.0;                 // (decrease_coeffs reads i < q - 1)
+            decrease_coeffs(tl.dec, nodes, e);
+            c.order_decrease(tl.dec, e);
+        }
+        if (tl.eta != 1.0) {
+            h *= tl.eta;
+            c.rescale(q, tl.eta);
+            if (tl.fail && t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); }
+        }
     }
 
     // the rarer outcomes of an attempt (out of line for C::kOutlineRare)
     __device__ __noinline__ void fail_newton_outlined(C &c) { fail_newton(c); }
-    __device__ __noinline__ void fail_error_outlined(C &c) { fail_error(c); }
+    __device__ __noinline__ void fail_error_outlined(C &c, Tail &tl) { fail_error(c, tl); }
     __device__ __forceinline__ void fail_newton(C &c)
     {
         c.unpredict(q);
@@ -542,7 +575,7 @@ struct CellRun {
         phase = PH_ATTEMPT;
     }
 
-    __device__ __forceinline__ void fail_error(C &c)
+    __device__ __forceinline__ void fail_error(C &c, Tail &tl)
     {
         {
             c.unpredict(q);
@@ -567,18 +600,26 @@ struct CellRun {
                 }
                 eta = fmin(ETA_MAX_EF, fmax(ETA_MIN_EF, eta));
                 if (newq < q) {
-                    double nodes[QMAX], sacc = 0.0, e[QMAX + 1];
-                    const double rh = rcp(h);
-                    for (int i = 0; i < QMAX; ++i) {
-                        sacc += hist[i];
-                        nodes[i] = sacc * rh;
+                    if constexpr (C::kSharedEtaQ) {
+                        tl.dec = q;
+                    } else {
+                        double nodes[QMAX], sacc = 0.0, e[QMAX + 1];
+                        const double rh = rcp(h);
+                        for (int i = 0; i < QMAX; ++i) {
+                            sacc += hist[i];
+                            nodes[i] = sacc * rh;
+                        }
+                        decrease_coeffs(q, nodes, e);
+                        c.order_decrease(q, e);
                     }
-                    decrease_coeffs(q, nodes, e);
-                    c.order_decrease(q, e);
                     q = newq; qwait = q + 1;
                 }
-                h *= eta;
-                c.rescale(q, eta);
+                if constexpr (C::kSharedEtaQ) {
+                    tl.eta = eta;
+                } else {
+                    h *= eta;
+                    c.rescale(q, eta);
+                }
             } else {
                 // third failure on: order 1 through the interpolating
                 // polynomials (keeps the line through the last two accepted
@@ -595,17 +636,25 @@ struct CellRun {
                         c.order_decrease(q, e);
                     }
                 }
-                h *= ETA_MIN_EF;
-                c.rescale(q, ETA_MIN_EF);
+                if constexpr (C::kSharedEtaQ) {
+                    tl.eta = ETA_MIN_EF;
+                } else {
+                    h *= ETA_MIN_EF;
+                    c.rescale(q, ETA_MIN_EF);
+                }
                 qwait = 2; have_ks = 0;
             }
             etamax = 1.0; last = 0; nsame = 0;
-            if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
             phase = PH_ATTEMPT;
+            if constexpr (C::kSharedEtaQ) {
+                tl.fail = 1;        // end_attempt rescales, then checks h
+            } else {
+                if (t + h == t) { s.status = ST_H_TOO_SMALL; finish(c); return; }
+            }
         }
     }
 
-    __device__ __forceinline__ void accept_step(C &c)
+    __device__ __forceinline__ void accept_step(C &c, Tail &tl)
     {
         s.nst++;
         t = last ? tout : t + h;
@@ -660,9 +709,13 @@ struct CellRun {
         c.rec_accept(q, newq == q + 1 ? q + 1 : q, l, inv_q, gamma, il1, h, ncf, nef);
         if (newq == q + 1) c.order_increase(q, l, inv_q);
         else if (newq == q - 1) {
-            double e[QMAX + 1];
-            decrease_coeffs(q, xi, e);
-            c.order_decrease(q, e);
+            if constexpr (C::kSharedEtaQ) {
+                tl.dec = q;
+            } else {
+                double e[QMAX + 1];
+                decrease_coeffs(q, xi, e);
+                c.order_decrease(q, e);
+            }
         }
         if (newq != q || qwait == 0) { q = newq; qwait = q + 1; have_ks = 0; }
         if (qwait == 1 && q < qmax) {
@@ -670,8 +723,12 @@ struct CellRun {
             h_ks = h; have_ks = 1;
         }
         if (eta != 1.0) {
-            h *= eta;
-            c.rescale(q, eta);
+            if constexpr (C::kSharedEtaQ) {
+                tl.eta = eta;
+            } else {
+                h *= eta;
+                c.rescale(q, eta);
+            }
             nsame = 0;
         } else if (nsame < QMAX) {
             ++nsame;

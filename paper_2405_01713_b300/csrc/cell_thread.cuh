@@ -41,6 +41,9 @@ struct RobertsonProblem {
     static constexpr int kNewtonPerSuperstep = MAXCOR;
     // cells of a one-wave launch all begin together: the start stays inline
     static constexpr bool kFoldedStart = false;
+    // a failed attempt subtracts the prediction back out (a saved copy of
+    // three-component columns would cost 36 registers)
+    static constexpr bool kSavedPrediction = false;
 };
 
 // Cooling table in shared memory: knots lnT[i], values lnLam[i] and the
@@ -125,6 +128,10 @@ struct CosmologyProblem {
     // a cell's start shares its warp's f evaluations (CellRun::begin_folded):
     // queue-fed warps begin cells at different supersteps
     static constexpr bool kFoldedStart = true;
+    // a failed attempt restores the Nordsieck array saved before the
+    // prediction (12 registers) instead of subtracting it back out: exact,
+    // and no FP64 work on a path that some cell of a warp nearly always takes
+    static constexpr bool kSavedPrediction = true;
     __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
     {
         eval(y[0], f[0], J[0][0]);
@@ -193,6 +200,7 @@ struct ThreadCell : ThreadTape<REC> {
     static constexpr bool kKrylov = false;
     Prob prob;
     double v[NVEC][N];
+    double zs[Prob::kSavedPrediction ? QMAX + 1 : 1][N];   // the array before predict()
     double M[N][N];
     double atol[N];
     double *yg;   // this cell's state in global memory
@@ -287,6 +295,12 @@ struct ThreadCell : ThreadTape<REC> {
     }
     __device__ __forceinline__ void predict(int q)
     {
+        if constexpr (Prob::kSavedPrediction) {
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) zs[j][i] = v[j][i];
+        }
 #pragma unroll
         for (int k = 0; k < QMAX; ++k)
 #pragma unroll
@@ -297,6 +311,13 @@ struct ThreadCell : ThreadTape<REC> {
     }
     __device__ __forceinline__ void unpredict(int q)
     {
+        if constexpr (Prob::kSavedPrediction) {
+#pragma unroll
+            for (int j = 0; j <= QMAX; ++j)
+#pragma unroll
+                for (int i = 0; i < N; ++i) v[j][i] = zs[j][i];
+            return;
+        }
 #pragma unroll
         for (int k = QMAX - 1; k >= 0; --k)
 #pragma unroll
