@@ -316,15 +316,15 @@ struct ThreadCell : ThreadTape<REC> {
             for (int j = 0; j <= QMAX; ++j)
 #pragma unroll
                 for (int i = 0; i < N; ++i) v[j][i] = zs[j][i];
-            return;
+        } else {
+#pragma unroll
+            for (int k = QMAX - 1; k >= 0; --k)
+#pragma unroll
+                for (int j = 1; j <= QMAX; ++j)
+                    if (k < q && j > k && j <= q)
+#pragma unroll
+                        for (int i = 0; i < N; ++i) v[j - 1][i] -= v[j][i];
         }
-#pragma unroll
-        for (int k = QMAX - 1; k >= 0; --k)
-#pragma unroll
-            for (int j = 1; j <= QMAX; ++j)
-                if (k < q && j > k && j <= q)
-#pragma unroll
-                    for (int i = 0; i < N; ++i) v[j - 1][i] -= v[j][i];
     }
     __device__ __forceinline__ void rescale(int q, double eta)
     {
