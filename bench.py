@@ -74,19 +74,21 @@ def jac_matrix_flops(mech):
 
 
 # DRAM bytes (read + write) per cell of one integrator launch, from one ncu
-# capture (--set full, one launch) of a smaller batch of the same kernel and
-# launch shape, scaled by cells (traffic is per cell: y in and out,
-# parameters, counters, and for the lane-group kernels the write-back of the
-# out-of-line calls' stack frames):
-#   ncu --set full --clock-control none -k regex:<kernel> -c 1 -o <report> \
+# capture (one launch) of a smaller batch of the same kernel and launch
+# shape, scaled by cells (traffic is per cell: y in and out, parameters,
+# counters, and for the lane-group kernels the write-back of the out-of-line
+# calls' stack frames):
+#   ncu --metrics dram__bytes_read.sum,dram__bytes_write.sum,gpu__time_duration.sum,\
+#       smsp__thread_inst_executed_per_inst_executed.ratio,\
+#       sm__pipe_fp64_cycles_active.avg.pct_of_peak_sustained_active \
+#       --clock-control none -k regex:<kernel> -c 1 --csv --log-file <csv> \
 #       python bench.py --workload <w> --cells <n> [--lanes <L>] --steps 1 --warmup 1 \
-#       --no-plain --no-cpu --no-e2e
-#   mech22, mech_kernel, 7168 cells, 8 lanes: 4.240 + 20.266 MB
-#   mech54, mech_kernel, 1480 cells, 32 lanes: 2.637 + 1.209 MB
-#   cosmology, thread_kernel, 2^20 cells: 27.141 + 7.857 MB (--metrics
-#       dram__bytes_read.sum,dram__bytes_write.sum instead of --set full)
-TRAFFIC_BYTES_PER_CELL = {"mech22": 24.505856e6 / 7168, "mech54": 3.845376e6 / 1480,
-                          "cosmology": 34.997504e6 / 1048576}
+#       [--no-plain] --no-cpu --no-e2e
+#   mech22, mech_kernel, 7168 cells, 8 lanes: 4.712 + 24.499 MB
+#   mech54, mech_kernel, 1480 cells, 32 lanes: 2.970 + 4.042 MB
+#   cosmology, thread_kernel, 2^20 cells: 28.500 + 9.679 MB
+TRAFFIC_BYTES_PER_CELL = {"mech22": 29.211392e6 / 7168, "mech54": 7.011840e6 / 1480,
+                          "cosmology": 38.179072e6 / 1048576}
 
 
 def work_model_split(kind, mech, tot, fp32_matrix=False, **kw):
