@@ -36,21 +36,35 @@
 
 namespace sunb {
 
-// xi_i (i = 1..m) from h and previous step sizes; inv[i-1] = 1/xi_i.
+// xi_i (i = 1..m) from h and previous step sizes: xi[i-1] = xi_i,
+// inv[i-1] = 1/xi_i; entries from m on are 1 (unused).  The inverses come
+// from one reciprocal (a batched inversion): with the running products
+// P_i = xi[1] ... xi[i], 1/xi[i] = P_{i-1} / P_i, taken from 1/P_QMAX
+// backwards.  Each carries a few roundings more than a division would, and
+// the FP64 pipe, the kernels' bound, sees one reciprocal instead of m - 1.
 __device__ __forceinline__ void bdf_xi(int m, double h, const double *hist, double *xi,
                                        double *inv)
 {
     const double rh = rcp(h);
-    double s = h;
+    double s = h, P[QMAX + 1];
     xi[0] = 1.0;
     inv[0] = 1.0;
+    P[0] = 1.0;
 #pragma unroll
     for (int i = 1; i < QMAX + 1; ++i) {
+        double x = 1.0;
         if (i < m) {
             s += hist[i - 1];
-            xi[i] = s * rh;
-            inv[i] = h * rcp(s);
+            x = s * rh;
         }
+        xi[i] = x;
+        P[i] = P[i - 1] * x;
+    }
+    double R = rcp(P[QMAX]);              // 1 / (xi[1] ... xi[QMAX])
+#pragma unroll
+    for (int i = QMAX; i >= 1; --i) {
+        inv[i] = R * P[i - 1];
+        R *= xi[i];
     }
 }
 
@@ -410,8 +424,11 @@ struct CellRun {
             } else {
                 bdf_xi(q + 1, h, hist, xi, inv);
                 bdf_l(q, inv, l);
-                il1 = rcp(l[1]);
-                Cq = rcp(1.0 + l[1] * pick(xi, q));
+                // 1/l_1 and C_q = 1/(1 + l_1 xi_{q+1}) from one reciprocal
+                const double cq1 = 1.0 + l[1] * pick(xi, q);
+                const double r = rcp(l[1] * cq1);
+                il1 = r * cq1;
+                Cq = r * l[1];
             }
             gamma = h * il1;
             fresh = 0;
