@@ -84,11 +84,13 @@ def jac_matrix_flops(mech):
 #       --clock-control none -k regex:<kernel> -c 1 --csv --log-file <csv> \
 #       python bench.py --workload <w> --cells <n> [--lanes <L>] --steps 1 --warmup 1 \
 #       [--no-plain] --no-cpu --no-e2e
-#   mech22, mech_kernel, 7168 cells, 8 lanes: 4.712 + 24.499 MB
-#   mech54, mech_kernel, 1480 cells, 32 lanes: 2.970 + 4.042 MB
-#   cosmology, thread_kernel, 2^20 cells: 28.500 + 9.679 MB
-TRAFFIC_BYTES_PER_CELL = {"mech22": 29.211392e6 / 7168, "mech54": 7.011840e6 / 1480,
-                          "cosmology": 38.179072e6 / 1048576}
+#   mech22, mech_kernel, 7168 cells, 8 lanes: 2.826 + 23.666 MB
+#   mech54, mech_kernel, 1480 cells, 32 lanes: 1.552 + 1.296 MB
+#   cosmology, thread_kernel, 2^20 cells: 28.291 + 9.887 MB
+# (the lane-group kernels' figures move between captures of one build by up
+# to 2.5x: the share of y and of the stack frames still in L2 varies)
+TRAFFIC_BYTES_PER_CELL = {"mech22": 26.492160e6 / 7168, "mech54": 2.848256e6 / 1480,
+                          "cosmology": 38.177792e6 / 1048576}
 
 
 def work_model_split(kind, mech, tot, fp32_matrix=False, **kw):
