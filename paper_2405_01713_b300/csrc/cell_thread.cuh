@@ -129,7 +129,7 @@ struct CosmologyProblem {
     // queue-fed warps begin cells at different supersteps
     static constexpr bool kFoldedStart = true;
     // a failed attempt restores the Nordsieck array saved before the
-    // prediction (12 registers) instead of subtracting it back out: exact,
+    // prediction (six doubles) instead of subtracting it back out: exact,
     // and no FP64 work on a path that some cell of a warp nearly always takes
     static constexpr bool kSavedPrediction = true;
     __device__ __forceinline__ void rhs_jac(const double *y, double *f, double (*J)[1]) const
