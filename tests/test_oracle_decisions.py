@@ -14,6 +14,7 @@ parity tests compare on).
   step-size and order choices.
 * The adjoint through a forced order drop from 5 to 1 (where the dropped
   column is large) matches central differences of the same map.
+* The step-size factors the oracle chooses are single-precision values.
 """
 import numpy as np
 import pytest
@@ -99,6 +100,26 @@ def test_map_from_decisions_equals_the_integrators_own(kind, cell):
         dL[:K] = 2.0 * (y1[:K] - 0.05)
         g1, g2 = oracle.adjoint_tape(pb, tp, dL, cell), oracle.adjoint_tape(pb, td, dL, cell)
         assert np.max(np.abs(g2 - g1).max(axis=0) / np.abs(g1).max(axis=0)) < 1e-10
+
+
+@pytest.mark.parametrize("kind,cell", [("mech22", 0), ("robertson", 2)])
+def test_step_factors_are_single_precision(kind, cell):
+    """The step-size factors are computed in single precision (the decisions
+    they make are taken in the CUDA path's precision).  After an accepted
+    step the factor is 1, a growth cap (10, or 1e4 after the first step,
+    both exact in float) or a float result, so every factor the oracle
+    chooses along its own run is a float value; factors strictly between
+    the threshold 1.5 and the cap occur, so the float results themselves are
+    checked."""
+    w = synth.workloads.mech22(2) if kind == "mech22" else synth.workloads.robertson(4)
+    pb, tp, r = _own_tape(w, cell)
+    tf = oracle.Tape.from_decisions(r["y0"], r["h0"], r["h"], r["q"], r["qo"], r["ncf"], r["nef"],
+                                    states=r["y"])
+    f = oracle.follow_tape(pb, tf, w["rtol"], w["atol"], cell)
+    eta = f["eta"][np.isfinite(f["eta"])]
+    inner = eta[(eta > 1.5) & (eta < 10.0)]
+    assert eta.size > 10 and inner.size > 3
+    np.testing.assert_array_equal(eta.astype(np.float32).astype(np.float64), eta)
 
 
 @pytest.mark.parametrize("kind,cell", [("mech22", 0), ("mech22", 1), ("robertson", 0), ("robertson", 2)])

@@ -97,6 +97,8 @@ MUTATIONS = [
      "for (int o = 0; o < 6; ++o) s += P[a * 6 + o] * lam[o * n + i];"),
     ("decision map rescaled by the inverse step ratio", "oracle.c",
      "tape_rescale(tp, q[r], h[r] / hprev);", "tape_rescale(tp, q[r], hprev / h[r]);"),
+    ("step-size factor in double precision", "oracle.c",
+     "return (double)(1.0f / (r + 1e-6f));", "return 1.0 / (pow(bias * dsm, 1.0 / (p + 1)) + 1e-6);"),
     ("following a run without restarting the order counter", "oracle.c",
      "if (qo == q + 1 || qwait == 0) { qwait = qo + 1; have_ks = 0; }", "if (qo == q + 1) { qwait = qo + 1; have_ks = 0; }"),
 ]
